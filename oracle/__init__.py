@@ -1,0 +1,187 @@
+"""FP64 CPU oracle for the LiFE hot path — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
+import this package.  The CUDA library never calls it and shares no code with it.
+
+Thin ctypes wrapper over ``oracle.c`` (plain double-precision loops written from
+the paper's definitions; see that file's header for the equation each routine
+follows).  Array conventions: D is a flat column-major vector ``D[θ + Nθ·a]``;
+signals are flat column-major ``y[θ + Nθ·v]``; Phi is four parallel COO arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+ORDER_VOXEL, ORDER_FIBER, ORDER_ATOM = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc, -O2, no FP contraction so both host ISAs round alike)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _SbbState(ctypes.Structure):
+    _fields_ = [("it", ctypes.c_int64), ("alpha", ctypes.c_double), ("obj", ctypes.c_double),
+                ("gg", ctypes.c_double), ("gg0", ctypes.c_double), ("vv", ctypes.c_double),
+                ("uu", ctypes.c_double), ("eq", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.oracle_dictionary.argtypes = [i32, i32, P, P, dbl, dbl, P, P]
+        lib.oracle_canon.argtypes = [i64, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i32,
+                                     P, P, P, P]
+        lib.oracle_canon.restype = i64
+        lib.oracle_dsc.argtypes = [i64, P, P, P, P, i32, P, P, i64, P]
+        lib.oracle_wc.argtypes = [i64, P, P, P, P, i32, P, P, i64, P]
+        lib.oracle_grad_D.argtypes = [i64, P, P, P, P, i32, i32, P, P, P]
+        lib.oracle_sbb_step.argtypes = [i64, P, P, P, P, i32, P, i64, i64, P, P, dbl, i32,
+                                        ctypes.POINTER(_SbbState), P]
+        lib.oracle_sbb_solve.argtypes = [i64, P, P, P, P, i32, P, i64, i64, P, P, dbl, i32, i64,
+                                         ctypes.POINTER(_SbbState), P]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+@dataclass
+class Phi:
+    """Phi as parallel COO arrays (atom, voxel, fascicle, value)."""
+    atom: np.ndarray
+    voxel: np.ndarray
+    fasc: np.ndarray
+    val: np.ndarray
+
+    def __len__(self):
+        return int(self.atom.shape[0])
+
+
+def dictionary(grad_dirs, atom_dirs, bval: float, lam: float):
+    """D (flat column-major, Nθ·Na) and dD/dλ, both demeaned per column."""
+    g, u = _f64(grad_dirs), _f64(atom_dirs)
+    nt, na = g.shape[0], u.shape[0]
+    D = np.empty(nt * na, np.float64)
+    dD = np.empty(nt * na, np.float64)
+    _load().oracle_dictionary(nt, na, _p(g), _p(u), float(bval), float(lam), _p(D), _p(dD))
+    return D, dD
+
+
+def canon(atom, voxel, fasc, val, n_atoms, n_voxels, n_fasc, order=ORDER_VOXEL) -> Phi:
+    """Restructured Phi: sorted by the chosen dimension, duplicates merged (FP64
+    sum, one rounding to float32)."""
+    a, v, f = _i32(atom), _i32(voxel), _i32(fasc)
+    x = np.ascontiguousarray(val, dtype=np.float32)
+    n = a.shape[0]
+    oa, ov, of = (np.empty(n, np.int32) for _ in range(3))
+    ox = np.empty(n, np.float32)
+    m = _load().oracle_canon(n, _p(a), _p(v), _p(f), _p(x), n_atoms, n_voxels, n_fasc, order,
+                             _p(oa), _p(ov), _p(of), _p(ox))
+    if m < 0:
+        raise ValueError("oracle_canon: index out of range or non-finite value")
+    return Phi(oa[:m].copy(), ov[:m].copy(), of[:m].copy(), ox[:m].copy())
+
+
+def dsc(phi: Phi, D, w, n_theta: int, n_voxels: int) -> np.ndarray:
+    """y = M w in FP64 (flat column-major)."""
+    y = np.empty(n_theta * n_voxels, np.float64)
+    val = _f64(phi.val)
+    _load().oracle_dsc(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)), _p(val),
+                       n_theta, _p(_f64(D)), _p(_f64(w)), n_voxels, _p(y))
+    return y
+
+
+def wc(phi: Phi, D, r, n_theta: int, n_fasc: int) -> np.ndarray:
+    """g = M^T r in FP64."""
+    g = np.empty(n_fasc, np.float64)
+    val = _f64(phi.val)
+    _load().oracle_wc(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)), _p(val),
+                      n_theta, _p(_f64(D)), _p(_f64(r)), n_fasc, _p(g))
+    return g
+
+
+def grad_D(phi: Phi, w, e, n_theta: int, n_atoms: int) -> np.ndarray:
+    """dL/dD (flat column-major) for L = ½‖r - M(D) w‖², given e = M w - r."""
+    gD = np.empty(n_theta * n_atoms, np.float64)
+    _load().oracle_grad_D(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
+                          _p(_f64(phi.val)), n_theta, n_atoms, _p(_f64(w)), _p(_f64(e)), _p(gD))
+    return gD
+
+
+def loss_grads(phi: Phi, D, dD_dlam, w, r, n_theta, n_atoms, n_voxels, n_fasc):
+    """L = ½‖r - M(D) w‖² and its gradients w.r.t. w, D and λ (through dD/dλ)."""
+    e = dsc(phi, D, w, n_theta, n_voxels) - _f64(r)
+    L = 0.5 * float(e @ e)
+    gw = wc(phi, D, e, n_theta, n_fasc)
+    gD = grad_D(phi, w, e, n_theta, n_atoms)
+    glam = float(gD @ _f64(dD_dlam))
+    return L, gw, gD, glam
+
+
+class SbbState:
+    """SBB-NNLS state: iteration count, last alpha, last dot products."""
+
+    def __init__(self):
+        self.s = _SbbState(it=0, alpha=1.0, obj=0.0, gg=0.0, gg0=0.0, vv=0.0, uu=0.0, eq=0, converged=0)
+
+    def __getattr__(self, k):
+        return getattr(self.__dict__["s"], k)
+
+    def as_dict(self):
+        return {k: getattr(self.s, k) for k, _ in _SbbState._fields_}
+
+
+def sbb_step(phi: Phi, D, b, w, n_theta, n_voxels, n_fasc, state: SbbState, tol=0.0, eq7_on_even=True):
+    """One SBB-NNLS iteration; updates ``w`` (float64 array) in place."""
+    assert w.dtype == np.float64 and w.flags.c_contiguous
+    work = np.empty(2 * n_theta * n_voxels + 2 * n_fasc, np.float64)
+    _load().oracle_sbb_step(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
+                            _p(_f64(phi.val)), n_theta, _p(_f64(D)), n_voxels, n_fasc, _p(_f64(b)), _p(w),
+                            float(tol), 1 if eq7_on_even else 0, ctypes.byref(state.s), _p(work))
+    return state
+
+
+def sbb_solve(phi: Phi, D, b, w, n_theta, n_voxels, n_fasc, max_iter, tol=0.0, eq7_on_even=True, state=None):
+    """Up to ``max_iter`` SBB-NNLS iterations from ``w`` (float64, updated in place)."""
+    state = state or SbbState()
+    assert w.dtype == np.float64 and w.flags.c_contiguous
+    work = np.empty(2 * n_theta * n_voxels + 2 * n_fasc, np.float64)
+    _load().oracle_sbb_solve(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
+                             _p(_f64(phi.val)), n_theta, _p(_f64(D)), n_voxels, n_fasc, _p(_f64(b)), _p(w),
+                             float(tol), 1 if eq7_on_even else 0, int(max_iter), ctypes.byref(state.s),
+                             _p(work))
+    return state
+
+
+def problem_signal(phi: Phi, D, w_true, noise, n_theta, n_voxels):
+    """b = M w_true + noise, rounded to float32 (the measured, demeaned signal)."""
+    return (dsc(phi, D, w_true, n_theta, n_voxels) + _f64(noise)).astype(np.float32)
