@@ -1,0 +1,233 @@
+/*
+ * liblife — GB300 (sm_103a) implementation of the LiFE hot path:
+ * the two Sparse-Tucker-Decomposed SpMVs and the SBB-NNLS loop around them.
+ *
+ * Model (Sec. 2.1, Eq. 1-4):  y ≈ M w,  M_v = S0(v) D Phi_v, stored as the sparse
+ * tensor Phi with coefficients (atom a, voxel v, fascicle f, value).  S0(v) is
+ * folded into the Phi values.  Dimensions: Nθ gradient directions, Na dictionary
+ * atoms, Nv voxels, Nf fascicles.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named in an argument list are DEVICE pointers owned by the caller,
+ *    unless the comment says "host".  The library owns only what a life_index holds.
+ *  - D is a float32 column-major dictionary, D[θ + Nθ·a].  Signals (y, b, r, e) are
+ *    float32 column-major [θ + Nθ·v].  Weights and fascicle vectors are float32 [f].
+ *  - Indices are 0-based int32.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) unless its comment says it synchronizes.  Outputs are overwritten,
+ *    never accumulated into.
+ *  - Calls that share one life_index must be ordered on one stream: the index owns
+ *    small reduction buffers that every SpMV call reuses.
+ *  - No call throws.  Each returns a life_status; on failure life_last_error()
+ *    gives a message (thread-local, valid until the next call on that thread).
+ */
+#ifndef LIFE_H
+#define LIFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LIFE_API __attribute__((visibility("default")))
+#else
+#define LIFE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LIFE_OK = 0,
+    LIFE_EINVAL = 1,    /* bad argument: null pointer, non-positive size, NaN/Inf value */
+    LIFE_ERANGE = 2,    /* an index outside [0, N) or a size beyond the supported range */
+    LIFE_ENOMEM = 3,    /* device allocation failed */
+    LIFE_ECUDA = 4,     /* a CUDA runtime call failed (message has the CUDA error) */
+    LIFE_ETIMEOUT = 5,  /* a bounded device-side wait gave up; results are invalid */
+    LIFE_ENOTSUP = 6    /* combination of options not supported by this build */
+} life_status;
+
+enum { LIFE_FP32 = 0, LIFE_BF16 = 1 };                 /* storage of Phi values and D */
+enum { LIFE_ALGO_AUTO = 0, LIFE_ALGO_SIMT = 1, LIFE_ALGO_TC = 2 };
+enum { LIFE_LAYOUT_VOXEL = 0, LIFE_LAYOUT_FIBER = 1, LIFE_LAYOUT_ATOM = 2 };
+
+typedef struct {
+    int32_t precision;     /* LIFE_FP32 (default) or LIFE_BF16 */
+    int32_t algo;          /* LIFE_ALGO_*: SIMT = CUDA-core kernels, TC = tensor-core kernels */
+    int32_t brick_dim;     /* TC path: edge of the cubic voxel brick used for locality (0 = 8) */
+    int32_t reserved[5];   /* must be zero */
+} life_opts;
+
+typedef struct life_index_s* life_index;
+
+typedef struct {
+    int64_t nnz_raw;       /* entries passed to life_build_index */
+    int64_t nnz;           /* distinct (a, v, f) entries after merging duplicates */
+    int32_t n_theta, n_atoms, n_voxels, n_fasc;
+    int32_t precision, algo;
+    int64_t n_tiles;       /* TC path: 128-voxel tiles; 0 otherwise */
+    int64_t n_bricks;      /* TC path: locality bricks; 0 otherwise */
+    int64_t device_bytes;  /* device memory held by the index */
+    int64_t stream_bytes;  /* bytes of Phi one SpMV streams from memory */
+} life_index_info;
+
+/*
+ * Data restructuring of Phi (Sec. 4.1.2): validates the COO list, merges entries
+ * with equal (a, v, f) (values summed in double precision, rounded once to
+ * float32), and builds the device layouts the SpMV kernels stream: a voxel-sorted
+ * CSR layout (voxel-based restructuring), and for the TC path a brick/tile layout
+ * sorted by (tile, atom, voxel, fascicle) with brick-local fascicle numbering.
+ *
+ *  atom, voxel, fasc, val   device, nnz entries each (the four Phi vectors, Sec. 2.2)
+ *  voxel_ijk                optional device int32 [Nv·3] grid coordinates (i, j, k)
+ *                           of each voxel; used only to group voxels into spatial
+ *                           bricks on the TC path; NULL keeps voxel-id order
+ *  opts                     host pointer or NULL for defaults
+ *  out                      host pointer receiving the new index
+ * Synchronizes `stream` (the merged size must reach the host to size the layouts).
+ * Errors: LIFE_EINVAL for null pointers, sizes < 1 (nnz may be 0) or a non-finite
+ * value; LIFE_ERANGE for an index outside its range or nnz >= 2^31.
+ */
+LIFE_API life_status life_build_index(const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
+                             const float* val, int64_t nnz, int32_t n_theta, int32_t n_atoms,
+                             int32_t n_voxels, int32_t n_fasc, const int32_t* voxel_ijk,
+                             const life_opts* opts, void* stream, life_index* out);
+
+/* Frees the index and its device memory (synchronizes the device). NULL is allowed. */
+LIFE_API life_status life_index_free(life_index idx);
+
+/* Sizes and layout facts of an index (host `out`). */
+LIFE_API life_status life_index_get_info(life_index idx, life_index_info* out);
+
+/*
+ * Writes the merged Phi in one of the paper's restructured orders (Sec. 4.1.2):
+ * LIFE_LAYOUT_VOXEL sorted by (v, a, f), LIFE_LAYOUT_FIBER by (f, v, a),
+ * LIFE_LAYOUT_ATOM by (a, v, f).  Device outputs of info.nnz entries each.
+ * Stored BF16 values are widened back to float32.  May allocate temporary device
+ * memory; synchronizes `stream`.
+ */
+LIFE_API life_status life_index_export(life_index idx, int32_t layout, int32_t* atom, int32_t* voxel,
+                              int32_t* fasc, float* val, void* stream);
+
+/*
+ * Copies the voxel-sorted streams the CUDA-core kernels read (voxel-based
+ * restructuring, Sec. 4.1.2): vox_ptr [Nv+1] (CSR offsets), atom, fasc, val
+ * [nnz] in (v, a, f) order.  Device outputs; stored BF16 values are widened.
+ * Any output may be NULL.  Synchronizes `stream`.
+ */
+LIFE_API life_status life_index_export_voxel_streams(life_index idx, int32_t* vox_ptr, int32_t* atom,
+                                                     int32_t* fasc, float* val, void* stream);
+
+/*
+ * DSC, y = M w (Sec. 4 "DSC"; Eq. 1 with Eq. 3-4):
+ *   y[θ,v] = Σ_{(a,v,f)∈Phi} D[θ,a] · val · w[f]   (minus b[θ,v] when b != NULL).
+ *  D      float32 [Nθ·Na] column-major
+ *  w      float32 [Nf]
+ *  b      float32 [Nθ·Nv] or NULL
+ *  y      float32 [Nθ·Nv] output, or NULL to compute only `sumsq`
+ *  sumsq  double [1] output, or NULL: Σ over all (θ,v) of the written y, in FP64
+ * Errors: LIFE_EINVAL when D, w or both y and sumsq are NULL.
+ */
+LIFE_API life_status life_dsc(life_index idx, const float* D, const float* w, const float* b, float* y,
+                     double* sumsq, void* stream);
+
+/*
+ * WC, g = M^T r (Sec. 4 "WC"; the transpose of Eq. 1):
+ *   g[f] = Σ_{(a,v,f)∈Phi} val · Σ_θ D[θ,a] · r[θ,v].
+ *  r      float32 [Nθ·Nv]
+ *  g      float32 [Nf] output (fully overwritten)
+ *  sumsq  double [1] output or NULL: Σ_f g[f]^2 in FP64
+ */
+LIFE_API life_status life_wc(life_index idx, const float* D, const float* r, float* g, double* sumsq,
+                    void* stream);
+
+/*
+ * Gradient of L with respect to the dictionary, for y = M(D) w and an upstream
+ * gradient gy = dL/dy (chain rule through Eq. 3): dL/dD[θ,a] = Σ_{(a,v,f)} val·w[f]·gy[θ,v].
+ *  gy  float32 [Nθ·Nv];  w float32 [Nf];  gD float32 [Nθ·Na] output.
+ * Deterministic: a fixed-order split over the atom-sorted Phi, no atomics.
+ */
+LIFE_API life_status life_dsc_grad_D(life_index idx, const float* gy, const float* w, float* gD, void* stream);
+
+/*
+ * Dictionary of canonical diffusion atoms (the D of Eq. 3) for the exponential
+ * atom model D_raw[θ,a] = exp(-bval·lam·(g_θ·u_a)^2), each column demeaned over θ,
+ * and its derivative dD/dlam (also demeaned).  Computed in double precision,
+ * stored as float32.
+ *  grad_dirs  double [Nθ·3] unit gradient directions (device)
+ *  atom_dirs  double [Na·3] unit atom orientations (device)
+ *  D, dD      float32 [Nθ·Na] outputs (dD may be NULL)
+ */
+LIFE_API life_status life_dictionary(int32_t n_theta, int32_t n_atoms, const double* grad_dirs,
+                            const double* atom_dirs, double bval, double lam, float* D, float* dD,
+                            void* stream);
+
+/* out[0] = Σ_{θ,a} gD[θ,a] · dD[θ,a] in FP64 (the chain rule from dL/dD to dL/dlam).
+ * n = Nθ·Na; out is a device double. */
+LIFE_API life_status life_dot_f32(int64_t n, const float* x, const float* y, double* out, void* stream);
+
+/* --------------------------------------------------------------- SBB-NNLS */
+
+/*
+ * SBB-NNLS state (Eq. 5-8, Algorithm 1), kept in DEVICE memory so the loop never
+ * synchronizes.  Zero it and set alpha = 1 before the first iteration
+ * (life_sbb_state_init does this).
+ */
+typedef struct {
+    int64_t it;          /* iterations taken (0-based index of the next iteration) */
+    double alpha;        /* last step size */
+    double obj;          /* ½‖M w − b‖² at the start of the last iteration */
+    double gg;           /* <g~, g~> at the start of the last iteration */
+    double gg0;          /* <g~, g~> at iteration 0 */
+    double vv;           /* <M g~, M g~> */
+    double uu;           /* <M^T M g~, M^T M g~> (Eq. 8 iterations) */
+    int32_t eq;          /* rule used last: 7 or 8 (0 when the iteration stopped early) */
+    int32_t converged;   /* 1 once <g~,g~> = 0 or ‖g~‖ <= tol ‖g~_0‖ */
+} life_sbb_state;
+
+/* Device bytes of the workspace one SBB call needs for this index. */
+LIFE_API life_status life_sbb_workspace_bytes(life_index idx, size_t* bytes);
+
+/* Writes {it=0, alpha=1, everything else 0} to the device state `st`. */
+LIFE_API life_status life_sbb_state_init(life_sbb_state* st, void* stream);
+
+/*
+ * One SBB-NNLS iteration on the device (Eq. 5-8, Algorithm 1):
+ *   e = M w − b, g = M^T e, g~ = g with g~_f = 0 where w_f = 0 and g_f > 0;
+ *   stop if <g~,g~> = 0 or ‖g~‖ <= tol·‖g~_0‖;
+ *   v' = M g~; Eq. 7 alpha = <g~,g~>/<v',v'> on even iterations (odd if
+ *   eq7_on_even = 0), else Eq. 8 alpha = <v',v'>/<v'',v''> with v'' = M^T v';
+ *   a zero denominator keeps the previous alpha; w = [w − alpha g~]_+.
+ * Vectors are float32; every dot product, alpha and the test are FP64.
+ *  b   float32 [Nθ·Nv];  w float32 [Nf] (updated in place);  st device state;
+ *  workspace  device, life_sbb_workspace_bytes() bytes, 256-byte aligned.
+ * A converged state makes the call a no-op.
+ */
+LIFE_API life_status life_sbbnnls_step(life_index idx, const float* D, const float* b, float* w,
+                              life_sbb_state* st, void* workspace, double tol, int32_t eq7_on_even,
+                              void* stream);
+
+/*
+ * Up to max_iter iterations of life_sbbnnls_step, replayed from a CUDA graph the
+ * index caches for these pointers.  With tol > 0 the host polls the state every
+ * 64 iterations (a stream synchronization) and stops early once converged.
+ */
+LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const float* b, float* w,
+                               int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
+                               void* workspace, void* stream);
+
+/* Checks the device status word every bounded wait in this library writes to;
+ * returns LIFE_ETIMEOUT (and clears the word) if one gave up.  Synchronizes. */
+LIFE_API life_status life_check_device_status(void* stream);
+
+/* Thread-local message for the last failed call on this thread ("" if none). */
+LIFE_API const char* life_last_error(void);
+
+/* Library version string. */
+LIFE_API const char* life_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIFE_H */

@@ -86,6 +86,9 @@ class Phi:
         return int(self.atom.shape[0])
 
 
+# Every wrapper below binds each converted array to a local name before the C
+# call, so that no temporary copy is freed while the C code still reads it.
+
 def dictionary(grad_dirs, atom_dirs, bval: float, lam: float):
     """D (flat column-major, Nθ·Na) and dD/dλ, both demeaned per column."""
     g, u = _f64(grad_dirs), _f64(atom_dirs)
@@ -111,29 +114,34 @@ def canon(atom, voxel, fasc, val, n_atoms, n_voxels, n_fasc, order=ORDER_VOXEL) 
     return Phi(oa[:m].copy(), ov[:m].copy(), of[:m].copy(), ox[:m].copy())
 
 
+def _phi_args(phi: Phi):
+    return _i32(phi.atom), _i32(phi.voxel), _i32(phi.fasc), _f64(phi.val)
+
+
 def dsc(phi: Phi, D, w, n_theta: int, n_voxels: int) -> np.ndarray:
     """y = M w in FP64 (flat column-major)."""
     y = np.empty(n_theta * n_voxels, np.float64)
-    val = _f64(phi.val)
-    _load().oracle_dsc(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)), _p(val),
-                       n_theta, _p(_f64(D)), _p(_f64(w)), n_voxels, _p(y))
+    a, v, f, val = _phi_args(phi)
+    Dd, wd = _f64(D), _f64(w)
+    _load().oracle_dsc(len(phi), _p(a), _p(v), _p(f), _p(val), n_theta, _p(Dd), _p(wd), n_voxels, _p(y))
     return y
 
 
 def wc(phi: Phi, D, r, n_theta: int, n_fasc: int) -> np.ndarray:
     """g = M^T r in FP64."""
     g = np.empty(n_fasc, np.float64)
-    val = _f64(phi.val)
-    _load().oracle_wc(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)), _p(val),
-                      n_theta, _p(_f64(D)), _p(_f64(r)), n_fasc, _p(g))
+    a, v, f, val = _phi_args(phi)
+    Dd, rd = _f64(D), _f64(r)
+    _load().oracle_wc(len(phi), _p(a), _p(v), _p(f), _p(val), n_theta, _p(Dd), _p(rd), n_fasc, _p(g))
     return g
 
 
 def grad_D(phi: Phi, w, e, n_theta: int, n_atoms: int) -> np.ndarray:
     """dL/dD (flat column-major) for L = ½‖r - M(D) w‖², given e = M w - r."""
     gD = np.empty(n_theta * n_atoms, np.float64)
-    _load().oracle_grad_D(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
-                          _p(_f64(phi.val)), n_theta, n_atoms, _p(_f64(w)), _p(_f64(e)), _p(gD))
+    a, v, f, val = _phi_args(phi)
+    wd, ed = _f64(w), _f64(e)
+    _load().oracle_grad_D(len(phi), _p(a), _p(v), _p(f), _p(val), n_theta, n_atoms, _p(wd), _p(ed), _p(gD))
     return gD
 
 
@@ -164,9 +172,10 @@ def sbb_step(phi: Phi, D, b, w, n_theta, n_voxels, n_fasc, state: SbbState, tol=
     """One SBB-NNLS iteration; updates ``w`` (float64 array) in place."""
     assert w.dtype == np.float64 and w.flags.c_contiguous
     work = np.empty(2 * n_theta * n_voxels + 2 * n_fasc, np.float64)
-    _load().oracle_sbb_step(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
-                            _p(_f64(phi.val)), n_theta, _p(_f64(D)), n_voxels, n_fasc, _p(_f64(b)), _p(w),
-                            float(tol), 1 if eq7_on_even else 0, ctypes.byref(state.s), _p(work))
+    a, v, f, val = _phi_args(phi)
+    Dd, bd = _f64(D), _f64(b)
+    _load().oracle_sbb_step(len(phi), _p(a), _p(v), _p(f), _p(val), n_theta, _p(Dd), n_voxels, n_fasc, _p(bd),
+                            _p(w), float(tol), 1 if eq7_on_even else 0, ctypes.byref(state.s), _p(work))
     return state
 
 
@@ -175,9 +184,10 @@ def sbb_solve(phi: Phi, D, b, w, n_theta, n_voxels, n_fasc, max_iter, tol=0.0, e
     state = state or SbbState()
     assert w.dtype == np.float64 and w.flags.c_contiguous
     work = np.empty(2 * n_theta * n_voxels + 2 * n_fasc, np.float64)
-    _load().oracle_sbb_solve(len(phi), _p(_i32(phi.atom)), _p(_i32(phi.voxel)), _p(_i32(phi.fasc)),
-                             _p(_f64(phi.val)), n_theta, _p(_f64(D)), n_voxels, n_fasc, _p(_f64(b)), _p(w),
-                             float(tol), 1 if eq7_on_even else 0, int(max_iter), ctypes.byref(state.s),
+    a, v, f, val = _phi_args(phi)
+    Dd, bd = _f64(D), _f64(b)
+    _load().oracle_sbb_solve(len(phi), _p(a), _p(v), _p(f), _p(val), n_theta, _p(Dd), n_voxels, n_fasc, _p(bd),
+                             _p(w), float(tol), 1 if eq7_on_even else 0, int(max_iter), ctypes.byref(state.s),
                              _p(work))
     return state
 

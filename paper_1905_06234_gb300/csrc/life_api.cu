@@ -1,0 +1,365 @@
+// C ABI of liblife: argument checking, index lifetime, dispatch to the SIMT or
+// tensor-core kernels, and the SBB-NNLS solve loop (graph-replayed).
+#include <cstdarg>
+#include <cstring>
+
+#include "life_internal.cuh"
+
+namespace life {
+
+static uint32_t* g_status_words[64] = {nullptr};
+
+uint32_t* dev_status_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_status_words[dev]) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(uint32_t));
+        g_status_words[dev] = static_cast<uint32_t*>(p);
+    }
+    return g_status_words[dev];
+}
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+size_t sbb_workspace_bytes(const life_index_s* ix);
+life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
+                             void* workspace, double tol, int eq7_on_even, cudaStream_t s);
+
+static bool use_tc(const life_index_s* ix) { return ix->algo == LIFE_ALGO_TC && ix->tile.built; }
+
+life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
+    if (use_tc(ix)) return dsc_tc(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+    return dsc_simt(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+}
+
+life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                    int gate_mode, cudaStream_t s) {
+    LIFE_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * (size_t)ix->nf, s));
+    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s);
+    return wc_simt(ix, D, r, g, gate, gate_mode, s);
+}
+
+}  // namespace life
+
+using namespace life;
+
+#define LIFE_VERSION "liblife 0.1 (sm_103a)"
+
+extern "C" const char* life_last_error(void) { return g_err; }
+extern "C" const char* life_version(void) { return LIFE_VERSION; }
+
+extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
+                                        const float* val, int64_t nnz, int32_t n_theta, int32_t n_atoms,
+                                        int32_t n_voxels, int32_t n_fasc, const int32_t* voxel_ijk,
+                                        const life_opts* opts, void* stream, life_index* out) {
+    g_err[0] = 0;
+    if (!out) {
+        set_error("life_build_index: null output pointer");
+        return LIFE_EINVAL;
+    }
+    *out = nullptr;
+    if (n_theta < 1 || n_atoms < 1 || n_voxels < 1 || n_fasc < 1 || nnz < 0) {
+        set_error("life_build_index: sizes must be positive (nnz >= 0)");
+        return LIFE_EINVAL;
+    }
+    if (nnz > 0 && (!atom || !voxel || !fasc || !val)) {
+        set_error("life_build_index: null Phi array");
+        return LIFE_EINVAL;
+    }
+    if (nnz >= (int64_t)INT32_MAX) {
+        set_error("life_build_index: nnz = %lld exceeds 2^31 - 1", (long long)nnz);
+        return LIFE_ERANGE;
+    }
+    if (n_atoms > 65535) {
+        set_error("life_build_index: n_atoms = %d exceeds 65535", n_atoms);
+        return LIFE_ERANGE;
+    }
+    life_opts o{};
+    if (opts) o = *opts;
+    for (int i = 0; i < 5; ++i)
+        if (o.reserved[i] != 0) {
+            set_error("life_build_index: reserved option fields must be zero");
+            return LIFE_EINVAL;
+        }
+    if (o.precision != LIFE_FP32 && o.precision != LIFE_BF16) {
+        set_error("life_build_index: unknown precision %d", o.precision);
+        return LIFE_EINVAL;
+    }
+    if (o.algo < LIFE_ALGO_AUTO || o.algo > LIFE_ALGO_TC) {
+        set_error("life_build_index: unknown algo %d", o.algo);
+        return LIFE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    life_index_s* ix = new (std::nothrow) life_index_s();
+    if (!ix) {
+        set_error("life_build_index: out of host memory");
+        return LIFE_ENOMEM;
+    }
+    ix->nt = n_theta;
+    ix->na = n_atoms;
+    ix->nv = n_voxels;
+    ix->nf = n_fasc;
+    ix->nnz_raw = nnz;
+    ix->precision = o.precision;
+    ix->brick_dim = o.brick_dim > 0 ? o.brick_dim : 8;
+    cudaGetDevice(&ix->device);
+    ix->num_sms = device_sm_count();
+    // The tensor-core path stores BF16; FP32 storage runs on CUDA cores.
+    int algo = o.algo;
+    if (algo == LIFE_ALGO_AUTO) algo = o.precision == LIFE_BF16 ? LIFE_ALGO_TC : LIFE_ALGO_SIMT;
+    if (algo == LIFE_ALGO_TC && o.precision != LIFE_BF16) {
+        delete ix;
+        set_error("life_build_index: the tensor-core path stores Phi and D in BF16 (precision = LIFE_BF16)");
+        return LIFE_ENOTSUP;
+    }
+    ix->algo = algo;
+    life_status st = build_voxel_layout(ix, atom, voxel, fasc, val, s);
+    if (st == LIFE_OK && voxel_ijk) {
+        st = ix->voxel_ijk.alloc(sizeof(int32_t) * 3 * (size_t)n_voxels);
+        if (st == LIFE_OK) {
+            cudaError_t e = cudaMemcpyAsync(ix->voxel_ijk.p, voxel_ijk, sizeof(int32_t) * 3 * (size_t)n_voxels,
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) {
+                set_error("life_build_index: %s", cudaGetErrorString(e));
+                st = LIFE_ECUDA;
+            }
+        }
+    }
+    if (st == LIFE_OK && algo == LIFE_ALGO_TC) {
+        st = build_tile_layout(ix, s);
+        if (st == LIFE_ENOTSUP && o.algo == LIFE_ALGO_AUTO) {
+            ix->algo = LIFE_ALGO_SIMT;  // AUTO falls back to the CUDA-core kernels
+            st = LIFE_OK;
+        }
+    }
+    if (st == LIFE_OK) st = ix->red.alloc(sizeof(double) * 4 * RED_SLOTS);
+    if (st == LIFE_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("life_build_index: %s", cudaGetErrorString(e));
+            st = LIFE_ECUDA;
+        }
+    }
+    if (st != LIFE_OK) {
+        delete ix;
+        return st;
+    }
+    *out = ix;
+    return LIFE_OK;
+}
+
+extern "C" life_status life_index_free(life_index idx) {
+    if (!idx) return LIFE_OK;
+    cudaDeviceSynchronize();
+    if (idx->graph) cudaGraphExecDestroy(idx->graph);
+    delete idx;
+    return LIFE_OK;
+}
+
+extern "C" life_status life_index_get_info(life_index idx, life_index_info* out) {
+    if (!idx || !out) {
+        set_error("life_index_get_info: null argument");
+        return LIFE_EINVAL;
+    }
+    life_index_info I{};
+    I.nnz_raw = idx->nnz_raw;
+    I.nnz = idx->nnz;
+    I.n_theta = idx->nt;
+    I.n_atoms = idx->na;
+    I.n_voxels = idx->nv;
+    I.n_fasc = idx->nf;
+    I.precision = idx->precision;
+    I.algo = idx->algo;
+    I.n_tiles = idx->tile.n_tiles;
+    I.n_bricks = idx->tile.n_bricks;
+    const DevBuf* bufs[] = {&idx->ukey, &idx->uval, &idx->voxel_ijk, &idx->vox.vox_ptr, &idx->vox.atom,
+                            &idx->vox.fasc, &idx->vox.val, &idx->atoml.voxel, &idx->atoml.fasc, &idx->atoml.val,
+                            &idx->atoml.chunk_beg, &idx->atoml.chunk_atom, &idx->atoml.atom_chunk,
+                            &idx->tile.tile_vox, &idx->tile.tile_chunk_ptr, &idx->tile.brick_tile_ptr,
+                            &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
+                            &idx->tile.va, &idx->tile.fl, &idx->tile.val, &idx->red};
+    int64_t tot = 0;
+    for (auto* b : bufs) tot += (int64_t)b->bytes;
+    I.device_bytes = tot;
+    if (idx->algo == LIFE_ALGO_TC && idx->tile.built)
+        I.stream_bytes = idx->tile.n_nnz * 6 + (int64_t)idx->tile.n_tiles * (TILE_V + idx->tile.n_kchunks + 1) * 4;
+    else
+        I.stream_bytes = idx->nnz * (2 + 4 + (idx->precision == LIFE_BF16 ? 2 : 4)) + 4 * ((int64_t)idx->nv + 1);
+    *out = I;
+    return LIFE_OK;
+}
+
+extern "C" life_status life_index_export(life_index idx, int32_t layout, int32_t* atom, int32_t* voxel,
+                                         int32_t* fasc, float* val, void* stream) {
+    if (!idx) {
+        set_error("life_index_export: null index");
+        return LIFE_EINVAL;
+    }
+    return export_layout(idx, layout, atom, voxel, fasc, val, (cudaStream_t)stream);
+}
+
+extern "C" life_status life_index_export_voxel_streams(life_index idx, int32_t* vox_ptr, int32_t* atom,
+                                                       int32_t* fasc, float* val, void* stream) {
+    if (!idx) {
+        set_error("life_index_export_voxel_streams: null index");
+        return LIFE_EINVAL;
+    }
+    return export_voxel_streams(idx, vox_ptr, atom, fasc, val, (cudaStream_t)stream);
+}
+
+extern "C" life_status life_dsc(life_index idx, const float* D, const float* w, const float* b, float* y,
+                                double* sumsq, void* stream) {
+    if (!idx || !D || !w || (!y && !sumsq)) {
+        set_error("life_dsc: null argument");
+        return LIFE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double* partial = idx->red.as<double>();
+    int np = 0;
+    LIFE_TRY(spmv_dsc(idx, D, w, b, y, partial, &np, nullptr, GATE_NONE, s));
+    if (sumsq) LIFE_TRY(reduce_partials(partial, np, sumsq, s));
+    return LIFE_OK;
+}
+
+extern "C" life_status life_wc(life_index idx, const float* D, const float* r, float* g, double* sumsq,
+                               void* stream) {
+    if (!idx || !D || !r || !g) {
+        set_error("life_wc: null argument");
+        return LIFE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    LIFE_TRY(spmv_wc(idx, D, r, g, nullptr, GATE_NONE, s));
+    if (sumsq) {
+        int np = 0;
+        double* partial = idx->red.as<double>() + RED_SLOTS;
+        LIFE_TRY(sumsq_f32(g, idx->nf, partial, &np, nullptr, GATE_NONE, s));
+        LIFE_TRY(reduce_partials(partial, np, sumsq, s));
+    }
+    return LIFE_OK;
+}
+
+extern "C" life_status life_dsc_grad_D(life_index idx, const float* gy, const float* w, float* gD, void* stream) {
+    if (!idx || !gy || !w || !gD) {
+        set_error("life_dsc_grad_D: null argument");
+        return LIFE_EINVAL;
+    }
+    return grad_D_simt(idx, gy, w, gD, (cudaStream_t)stream);
+}
+
+extern "C" life_status life_sbb_workspace_bytes(life_index idx, size_t* bytes) {
+    if (!idx || !bytes) {
+        set_error("life_sbb_workspace_bytes: null argument");
+        return LIFE_EINVAL;
+    }
+    *bytes = sbb_workspace_bytes(idx);
+    return LIFE_OK;
+}
+
+static life_status check_sbb_args(life_index idx, const float* D, const float* b, float* w, life_sbb_state* st,
+                                  void* ws, const char* who) {
+    if (!idx || !D || !b || !w || !st || !ws) {
+        set_error("%s: null argument", who);
+        return LIFE_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) {
+        set_error("%s: workspace must be 256-byte aligned", who);
+        return LIFE_EINVAL;
+    }
+    return LIFE_OK;
+}
+
+extern "C" life_status life_sbbnnls_step(life_index idx, const float* D, const float* b, float* w,
+                                         life_sbb_state* st, void* workspace, double tol, int32_t eq7_on_even,
+                                         void* stream) {
+    LIFE_TRY(check_sbb_args(idx, D, b, w, st, workspace, "life_sbbnnls_step"));
+    return sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, (cudaStream_t)stream);
+}
+
+extern "C" life_status life_sbbnnls_solve(life_index idx, const float* D, const float* b, float* w,
+                                          int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
+                                          void* workspace, void* stream) {
+    LIFE_TRY(check_sbb_args(idx, D, b, w, st, workspace, "life_sbbnnls_solve"));
+    if (max_iter <= 0) return LIFE_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void* key[8] = {D, b, w, st, workspace, stream, nullptr, nullptr};
+    bool same = idx->graph && idx->graph_tol == tol && idx->graph_eq7 == eq7_on_even &&
+                std::memcmp(key, idx->graph_key, sizeof(key)) == 0;
+    if (!same) {
+        if (idx->graph) {
+            cudaGraphExecDestroy(idx->graph);
+            idx->graph = nullptr;
+        }
+        // Capture on a private stream so that a caller on the legacy default
+        // stream can still use the graph.
+        cudaStream_t cap;
+        LIFE_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        LIFE_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        life_status est = sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (est != LIFE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return est;
+        }
+        if (ce != cudaSuccess) {
+            set_error("life_sbbnnls_solve: graph capture failed: %s", cudaGetErrorString(ce));
+            return LIFE_ECUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&idx->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            idx->graph = nullptr;
+            set_error("life_sbbnnls_solve: graph instantiate failed: %s", cudaGetErrorString(ie));
+            return LIFE_ECUDA;
+        }
+        std::memcpy(idx->graph_key, key, sizeof(key));
+        idx->graph_tol = tol;
+        idx->graph_eq7 = eq7_on_even;
+    }
+    life_sbb_state hst;
+    for (int64_t i = 0; i < max_iter; ++i) {
+        LIFE_CUDA_TRY(cudaGraphLaunch(idx->graph, s));
+        if (tol > 0.0 && ((i + 1) % 64) == 0 && i + 1 < max_iter) {
+            LIFE_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+            LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hst.converged) break;
+        }
+    }
+    return LIFE_OK;
+}
+
+extern "C" life_status life_check_device_status(void* stream) {
+    uint32_t v = 0;
+    uint32_t* word = dev_status_word();
+    if (!word) {
+        set_error("life_check_device_status: cannot allocate the status word");
+        return LIFE_ENOMEM;
+    }
+    LIFE_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    LIFE_CUDA_TRY(cudaMemcpy(&v, word, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v & DEV_TIMEOUT) {
+        LIFE_CUDA_TRY(cudaMemset(word, 0, sizeof(uint32_t)));
+        set_error("a bounded device-side wait timed out; the last results are invalid");
+        return LIFE_ETIMEOUT;
+    }
+    return LIFE_OK;
+}

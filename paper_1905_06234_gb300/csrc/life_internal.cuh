@@ -1,0 +1,219 @@
+// Internal declarations shared by the liblife translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/life.h"
+
+namespace life {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+
+struct Err {
+    life_status st;
+};
+
+#define LIFE_CUDA_TRY(expr)                                                                     \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            ::life::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? LIFE_ENOMEM : LIFE_ECUDA;                   \
+        }                                                                                        \
+    } while (0)
+
+#define LIFE_TRY(expr)                      \
+    do {                                    \
+        life_status s_ = (expr);            \
+        if (s_ != LIFE_OK) return s_;       \
+    } while (0)
+
+#define LIFE_CHECK_LAUNCH() LIFE_CUDA_TRY(cudaGetLastError())
+
+// Device-side status word (bounded waits record a timeout here, never trap).
+enum : uint32_t { DEV_OK = 0, DEV_TIMEOUT = 1u, DEV_BAD_INDEX = 2u, DEV_BAD_VALUE = 4u };
+// Device word that bounded waits set (per device, allocated on first use).
+uint32_t* dev_status_word();
+
+// ----------------------------------------------------------- device buffers
+
+// Owning device allocation (cudaMalloc; freed in the destructor).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    life_status alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+            return LIFE_ENOMEM;
+        }
+        bytes = n;
+        return LIFE_OK;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync on one stream).
+struct TmpBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    TmpBuf() = default;
+    TmpBuf(const TmpBuf&) = delete;
+    TmpBuf& operator=(const TmpBuf&) = delete;
+    ~TmpBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    life_status alloc(size_t n, cudaStream_t st) {
+        s = st;
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMallocAsync(&p, n, st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMallocAsync(%zu) failed: %s", n, cudaGetErrorString(e));
+            return LIFE_ENOMEM;
+        }
+        return LIFE_OK;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------ layouts
+
+constexpr int TILE_V = 128;        // voxels per tensor-core tile (MMA M)
+constexpr int KCHUNK = 64;         // atoms per K chunk of the tile layout
+constexpr int MAX_BRICK_FASC = 16384;  // brick-local fascicle table capacity (64 KB of FP32)
+constexpr int RED_SLOTS = 4096;    // per-call FP64 partial-sum slots
+
+// SIMT path: voxel-sorted CSR, (v, a, f) order.
+struct VoxelLayout {
+    DevBuf vox_ptr;   // int32 [Nv+1]
+    DevBuf atom;      // uint16 [nnz]
+    DevBuf fasc;      // int32 [nnz]
+    DevBuf val;       // float [nnz] or bf16 [nnz]
+};
+
+// Atom-sorted chunks for the deterministic dL/dD split (a, v, f) order.
+struct AtomLayout {
+    bool built = false;
+    DevBuf voxel;       // int32 [nnz]
+    DevBuf fasc;        // int32 [nnz]
+    DevBuf val;         // float [nnz]
+    DevBuf chunk_beg;   // int32 [n_chunks+1] nonzero offsets; every chunk lies in one atom
+    DevBuf chunk_atom;  // int32 [n_chunks]
+    DevBuf atom_chunk;  // int32 [Na+1] chunk offsets per atom
+    int32_t n_chunks = 0;
+};
+
+// TC path: bricks of voxel tiles with brick-local fascicle numbering.
+struct TileLayout {
+    bool built = false;
+    int64_t n_tiles = 0, n_bricks = 0, n_nnz = 0;   // n_nnz includes alignment padding
+    int32_t n_kchunks = 0;                           // ceil(Na / KCHUNK)
+    DevBuf tile_vox;        // int32 [n_tiles * TILE_V] voxel id per tile row (-1 = padding)
+    DevBuf tile_chunk_ptr;  // int32 [n_tiles * (n_kchunks+1)] nonzero offsets per (tile, chunk)
+    DevBuf brick_tile_ptr;  // int32 [n_bricks+1] tiles of each brick (consecutive)
+    DevBuf brick_fasc_ptr;  // int32 [n_bricks+1] offsets into brick_fasc
+    DevBuf brick_fasc;      // int32 [sum] global fascicle id of each brick-local fascicle
+    DevBuf brick_order;     // int32 [n_bricks] processing order (largest first)
+    DevBuf va;              // uint16 [n_nnz]: v_local | (a << 7)
+    DevBuf fl;              // uint16 [n_nnz]: brick-local fascicle
+    DevBuf val;             // bf16 [n_nnz]
+};
+
+}  // namespace life
+
+struct life_index_s {
+    int32_t nt = 0, na = 0, nv = 0, nf = 0;
+    int64_t nnz_raw = 0, nnz = 0;
+    int32_t precision = LIFE_FP32, algo = LIFE_ALGO_SIMT, brick_dim = 8;
+    int32_t key_bits_v = 0, key_bits_a = 0, key_bits_f = 0;
+    int device = 0;
+    int num_sms = 0;
+    life::DevBuf ukey;          // uint64 [nnz] merged keys in (v, a, f) order
+    life::DevBuf uval;          // float [nnz] merged values
+    life::DevBuf voxel_ijk;     // int32 [Nv*3] copy (optional)
+    life::VoxelLayout vox;
+    life::AtomLayout atoml;
+    life::TileLayout tile;
+    life::DevBuf red;           // double [4 * RED_SLOTS] partial sums
+    // cached solve graph
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_key[8] = {nullptr};
+    double graph_tol = -1.0;
+    int graph_eq7 = -1;
+};
+
+namespace life {
+
+// -------------------------------------------------------------- index build
+life_status build_voxel_layout(life_index_s* ix, const int32_t* atom, const int32_t* voxel,
+                               const int32_t* fasc, const float* val, cudaStream_t s);
+life_status build_atom_layout(life_index_s* ix, cudaStream_t s);
+life_status build_tile_layout(life_index_s* ix, cudaStream_t s);
+life_status export_voxel_streams(life_index_s* ix, int32_t* vox_ptr, int32_t* atom, int32_t* fasc,
+                                 float* val, cudaStream_t s);
+life_status export_layout(life_index_s* ix, int layout, int32_t* atom, int32_t* voxel, int32_t* fasc,
+                          float* val, cudaStream_t s);
+
+// Sorting and scans (index_build.cu)
+life_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
+life_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------ SIMT SpMVs
+// `partial` receives one FP64 partial sum per block (n_partial blocks).
+life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
+                     double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
+                     cudaStream_t s);
+life_status wc_simt(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                    int gate_mode, cudaStream_t s);
+life_status grad_D_simt(life_index_s* ix, const float* gy, const float* w, float* gD, cudaStream_t s);
+
+// -------------------------------------------------------------- TC SpMVs
+life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
+                   double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
+                   cudaStream_t s);
+life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                  int gate_mode, cudaStream_t s);
+
+// ------------------------------------------------------------ reductions
+// Sums `n` partial FP64 values into *out with one block (fixed order).
+life_status reduce_partials(const double* partial, int n, double* out, cudaStream_t s);
+life_status sumsq_f32(const float* x, int64_t n, double* partial, int* n_partial,
+                      const life_sbb_state* gate, int gate_mode, cudaStream_t s);
+
+// Gate modes: kernels read the device SBB state and return early.
+enum GateMode : int {
+    GATE_NONE = 0,       // always run
+    GATE_ACTIVE = 1,     // skip when converged
+    GATE_EQ8 = 2,        // skip when converged or this iteration uses Eq. 7
+};
+
+__device__ __forceinline__ bool gate_skip(const life_sbb_state* st, int mode) {
+    if (mode == GATE_NONE || st == nullptr) return false;
+    if (st->converged) return true;
+    if (mode == GATE_EQ8 && st->eq != 8) return true;
+    return false;
+}
+
+int device_sm_count();
+
+}  // namespace life

@@ -1,0 +1,306 @@
+// SBB-NNLS on the device (Eq. 5-8, Algorithm 1), FP64 reductions, and the
+// dictionary of diffusion atoms (the D of Eq. 3) with its λ-derivative.
+//
+// One iteration is a fixed sequence of launches; the iteration's decisions
+// (stop / Eq. 7 / Eq. 8) live in the device state, and every later kernel reads
+// that state and returns early when it has nothing to do.  The host never
+// synchronizes inside the loop, so a whole iteration can be captured in a graph.
+#include "life_internal.cuh"
+
+namespace life {
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block sum (deterministic for a fixed launch shape).
+__device__ double block_reduce(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;  // valid in thread 0
+}
+
+__device__ double sum_partials(const double* p, int n) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    return block_reduce(s);
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ p, int n, double* __restrict__ out) {
+    const double t = sum_partials(p, n);
+    if (threadIdx.x == 0) *out = t;
+}
+
+life_status reduce_partials(const double* partial, int n, double* out, cudaStream_t s) {
+    reduce_partials_kernel<<<1, RED_THREADS, 0, s>>>(partial, n, out);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+__global__ void sumsq_f32_kernel(const float* __restrict__ x, int64_t n, double* __restrict__ partial,
+                                 const life_sbb_state* gate, int gate_mode) {
+    if (gate_skip(gate, gate_mode)) return;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        s += v * v;
+    }
+    const double t = block_reduce(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+life_status sumsq_f32(const float* x, int64_t n, double* partial, int* n_partial, const life_sbb_state* gate,
+                      int gate_mode, cudaStream_t s) {
+    const int grid = device_sm_count() * 2;
+    sumsq_f32_kernel<<<grid, RED_THREADS, 0, s>>>(x, n, partial, gate, gate_mode);
+    LIFE_CHECK_LAUNCH();
+    *n_partial = grid;
+    return LIFE_OK;
+}
+
+__global__ void dot_f32_kernel(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
+                               double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * (double)y[i];
+    const double t = block_reduce(s);
+    if (threadIdx.x == 0) *out = t;
+}
+
+// ---------------------------------------------------------------- SBB steps
+
+// g~_f = g_f unless w_f = 0 and g_f > 0 (subspace projection); Σ g~² per block.
+__global__ void sbb_project_kernel(const float* __restrict__ w, const float* __restrict__ g,
+                                   float* __restrict__ gt, int64_t nf, double* __restrict__ partial,
+                                   const life_sbb_state* st) {
+    if (st->converged) return;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float v = (w[i] == 0.0f && gi > 0.0f) ? 0.0f : gi;
+        gt[i] = v;
+        s += (double)v * (double)v;
+    }
+    const double t = block_reduce(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// obj, <g~,g~>, the stopping test and this iteration's step rule (one block).
+__global__ void sbb_scalars1_kernel(life_sbb_state* st, const double* __restrict__ pe, int ne,
+                                    const double* __restrict__ pg, int ng, double tol, int eq7_on_even) {
+    if (st->converged) return;
+    const double ee = sum_partials(pe, ne);
+    __syncthreads();
+    const double gg = sum_partials(pg, ng);
+    if (threadIdx.x != 0) return;
+    st->obj = 0.5 * ee;
+    st->gg = gg;
+    if (st->it == 0) st->gg0 = gg;
+    if (gg == 0.0 || sqrt(gg) <= tol * sqrt(st->gg0)) {
+        st->converged = 1;
+        st->eq = 0;
+        return;
+    }
+    const bool even = (st->it & 1) == 0;
+    st->eq = (eq7_on_even ? even : !even) ? 7 : 8;
+}
+
+// <v',v'>, <v'',v''>, the step size (Eq. 7 or Eq. 8), and the iteration count.
+__global__ void sbb_scalars2_kernel(life_sbb_state* st, const double* __restrict__ pv, int nv_,
+                                    const double* __restrict__ pu, int nu) {
+    if (st->converged) return;
+    const double vv = sum_partials(pv, nv_);
+    __syncthreads();
+    double uu = 0.0;
+    if (st->eq == 8) uu = sum_partials(pu, nu);
+    if (threadIdx.x != 0) return;
+    double alpha = st->alpha;
+    if (st->eq == 7) {
+        if (vv > 0.0) alpha = st->gg / vv;   // Eq. 7
+    } else {
+        if (uu > 0.0) alpha = vv / uu;       // Eq. 8
+    }
+    st->vv = vv;
+    st->uu = uu;
+    st->alpha = alpha;
+    st->it += 1;
+}
+
+// w = [w − alpha g~]_+  (Eq. 5)
+__global__ void sbb_update_kernel(float* __restrict__ w, const float* __restrict__ gt, int64_t nf,
+                                  const life_sbb_state* st) {
+    if (st->converged) return;
+    const float alpha = (float)st->alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = fmaf(-alpha, gt[i], w[i]);
+        w[i] = x > 0.0f ? x : 0.0f;
+    }
+}
+
+__global__ void sbb_init_kernel(life_sbb_state* st) {
+    st->it = 0;
+    st->alpha = 1.0;
+    st->obj = st->gg = st->gg0 = st->vv = st->uu = 0.0;
+    st->eq = 0;
+    st->converged = 0;
+}
+
+// ------------------------------------------------------------- dictionary
+
+// One block per atom: D_raw in FP64, column mean over θ, demeaned float32 output.
+__global__ void dictionary_kernel(int nt, int na, const double* __restrict__ g, const double* __restrict__ u,
+                                  double bval, double lam, float* __restrict__ D, float* __restrict__ dD) {
+    const int a = blockIdx.x;
+    if (a >= na) return;
+    const double ux = u[3 * a], uy = u[3 * a + 1], uz = u[3 * a + 2];
+    double s = 0.0, sd = 0.0;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const double c = g[3 * t] * ux + g[3 * t + 1] * uy + g[3 * t + 2] * uz;
+        const double e = exp(-bval * lam * c * c);
+        s += e;
+        sd += -bval * c * c * e;
+    }
+    __shared__ double mean[2];
+    const double ts = block_reduce(s);
+    __syncthreads();
+    const double tsd = block_reduce(sd);
+    if (threadIdx.x == 0) {
+        mean[0] = ts / nt;
+        mean[1] = tsd / nt;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const double c = g[3 * t] * ux + g[3 * t + 1] * uy + g[3 * t + 2] * uz;
+        const double e = exp(-bval * lam * c * c);
+        D[t + (int64_t)nt * a] = (float)(e - mean[0]);
+        if (dD) dD[t + (int64_t)nt * a] = (float)(-bval * c * c * e - mean[1]);
+    }
+}
+
+}  // namespace life
+
+using namespace life;
+
+// ------------------------------------------------------------------ C ABI
+
+static life_status check_stream_ok(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return LIFE_ECUDA;
+    }
+    return LIFE_OK;
+}
+
+extern "C" life_status life_dictionary(int32_t n_theta, int32_t n_atoms, const double* grad_dirs,
+                                       const double* atom_dirs, double bval, double lam, float* D, float* dD,
+                                       void* stream) {
+    if (n_theta < 1 || n_atoms < 1 || !grad_dirs || !atom_dirs || !D) {
+        set_error("life_dictionary: bad argument");
+        return LIFE_EINVAL;
+    }
+    dictionary_kernel<<<n_atoms, 128, 0, (cudaStream_t)stream>>>(n_theta, n_atoms, grad_dirs, atom_dirs, bval, lam,
+                                                                 D, dD);
+    return check_stream_ok("life_dictionary");
+}
+
+extern "C" life_status life_dot_f32(int64_t n, const float* x, const float* y, double* out, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y)) || !out) {
+        set_error("life_dot_f32: bad argument");
+        return LIFE_EINVAL;
+    }
+    dot_f32_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(x, y, n, out);
+    return check_stream_ok("life_dot_f32");
+}
+
+extern "C" life_status life_sbb_state_init(life_sbb_state* st, void* stream) {
+    if (!st) {
+        set_error("life_sbb_state_init: null state");
+        return LIFE_EINVAL;
+    }
+    sbb_init_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(st);
+    return check_stream_ok("life_sbb_state_init");
+}
+
+namespace life {
+
+struct SbbWork {
+    float* e;       // [nt*nv] residual, then v' = M g~
+    float* g;       // [nf] gradient
+    float* gt;      // [nf] projected gradient
+    float* u;       // [nf] v'' = M^T v'
+    double* pe;     // partials
+    double* pg;
+    double* pv;
+    double* pu;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t sbb_workspace_bytes(const life_index_s* ix) {
+    const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf;
+    return align256(ny * 4) + 3 * align256(nf * 4) + 4 * align256(RED_SLOTS * 8);
+}
+
+static SbbWork carve(const life_index_s* ix, void* ws) {
+    char* p = static_cast<char*>(ws);
+    const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf;
+    SbbWork W;
+    W.e = reinterpret_cast<float*>(p); p += align256(ny * 4);
+    W.g = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.gt = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.u = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.pe = reinterpret_cast<double*>(p); p += align256(RED_SLOTS * 8);
+    W.pg = reinterpret_cast<double*>(p); p += align256(RED_SLOTS * 8);
+    W.pv = reinterpret_cast<double*>(p); p += align256(RED_SLOTS * 8);
+    W.pu = reinterpret_cast<double*>(p);
+    return W;
+}
+
+life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s);
+life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                    int gate_mode, cudaStream_t s);
+
+// Enqueues one SBB-NNLS iteration (no host synchronization).
+life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
+                             void* workspace, double tol, int eq7_on_even, cudaStream_t s) {
+    SbbWork W = carve(ix, workspace);
+    const int64_t ny = (int64_t)ix->nt * ix->nv, nf = ix->nf;
+    const int vgrid = std::min(device_sm_count() * 4, RED_SLOTS);
+    int ne = 0, nv_ = 0, nu = 0;
+    // e = M w − b, Σ e²
+    LIFE_TRY(spmv_dsc(ix, D, w, b, W.e, W.pe, &ne, st, GATE_ACTIVE, s));
+    // g = M^T e
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s));
+    // g~, Σ g~²
+    sbb_project_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, W.g, W.gt, nf, W.pg, st);
+    LIFE_CHECK_LAUNCH();
+    sbb_scalars1_kernel<<<1, RED_THREADS, 0, s>>>(st, W.pe, ne, W.pg, vgrid, tol, eq7_on_even);
+    LIFE_CHECK_LAUNCH();
+    // v' = M g~ (stored only on Eq. 8 iterations), Σ v'²
+    LIFE_TRY(spmv_dsc(ix, D, W.gt, nullptr, W.e, W.pv, &nv_, st, 3, s));
+    // v'' = M^T v', Σ v''² (Eq. 8 iterations only)
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s));
+    LIFE_TRY(sumsq_f32(W.u, nf, W.pu, &nu, st, GATE_EQ8, s));
+    sbb_scalars2_kernel<<<1, RED_THREADS, 0, s>>>(st, W.pv, nv_, W.pu, nu);
+    LIFE_CHECK_LAUNCH();
+    sbb_update_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, W.gt, nf, st);
+    LIFE_CHECK_LAUNCH();
+    (void)ny;
+    return LIFE_OK;
+}
+
+}  // namespace life

@@ -1,0 +1,327 @@
+// CUDA-core FP32 SpMVs on the voxel-sorted layout.
+//
+// DSC (y = M w) and WC (g = M^T r) as in Sec. 4.2.2 (GPU-specific optimizations):
+// voxel-based restructuring and partitioning, one warp per voxel segment, the
+// Nθ loop spread over the 32 lanes (Nθ padded to a multiple of 32 inside the
+// kernel), the dictionary D staged in shared memory, and zero val·w products
+// skipped (Sec. 4.2.1, "BLAS call for DSC").  WC reduces each warp's 32 dot
+// products with a transpose-reduction of shuffles and adds val·dot into g[f]
+// with one atomic per nonzero (the paper's coefficient-based WC also uses atomics).
+#include "life_internal.cuh"
+
+namespace life {
+
+constexpr int SIMT_THREADS = 1024;
+constexpr size_t SIMT_SMEM_LIMIT = 200 * 1024;
+
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+template <int NTW>
+__device__ __forceinline__ void stage_D(float* Ds, const float* __restrict__ D, int nt, int na) {
+    const int ntp = NTW * 32;
+    for (int i = threadIdx.x; i < na * ntp; i += blockDim.x) {
+        const int a = i / ntp, t = i - a * ntp;
+        Ds[i] = t < nt ? D[t + (int64_t)nt * a] : 0.0f;
+    }
+}
+
+template <class VT>
+__device__ __forceinline__ float ldval(const VT* p, int64_t k);
+template <>
+__device__ __forceinline__ float ldval<float>(const float* p, int64_t k) { return __ldg(p + k); }
+template <>
+__device__ __forceinline__ float ldval<__nv_bfloat16>(const __nv_bfloat16* p, int64_t k) {
+    return __bfloat162float(p[k]);
+}
+
+// y[:,v] = Σ_k D[:,a_k] val_k w[f_k]  (− b[:,v]);  per-block FP64 Σ out².
+template <int NTW, bool SMEM_D, class VT>
+__global__ void __launch_bounds__(SIMT_THREADS)
+dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
+                const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D,
+                int nt, int na, int nv, const float* __restrict__ w, const float* __restrict__ b,
+                float* __restrict__ y, double* __restrict__ partial, const life_sbb_state* gate, int gate_mode) {
+    extern __shared__ float Ds[];
+    __shared__ double red[32];
+    if (gate_skip(gate, gate_mode)) return;
+    bool write_y = y != nullptr;
+    if (gate && gate_mode == 3 && gate->eq != 8) write_y = false;
+    constexpr int NTP = NTW * 32;
+    if (SMEM_D) {
+        stage_D<NTW>(Ds, D, nt, na);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    double sq = 0.0;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+        float acc[NTW];
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) acc[q] = 0.0f;
+        const int beg = vox_ptr[v], end = vox_ptr[v + 1];
+        for (int base = beg; base < end; base += 32) {
+            const int k = base + lane;
+            int a_l = 0;
+            float s_l = 0.0f;
+            if (k < end) {
+                a_l = atom[k];
+                s_l = ldval<VT>(val, k) * __ldg(w + fasc[k]);
+            }
+            const int cnt = min(32, end - base);
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float s = __shfl_sync(0xffffffffu, s_l, j);
+                const int a = __shfl_sync(0xffffffffu, a_l, j);
+                if (s != 0.0f) {
+                    if (SMEM_D) {
+                        const float* d = Ds + a * NTP + lane;
+#pragma unroll
+                        for (int q = 0; q < NTW; ++q) acc[q] = fmaf(d[q * 32], s, acc[q]);
+                    } else {
+                        const float* d = D + (int64_t)nt * a;
+#pragma unroll
+                        for (int q = 0; q < NTW; ++q) {
+                            const int t = q * 32 + lane;
+                            acc[q] = fmaf(t < nt ? __ldg(d + t) : 0.0f, s, acc[q]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) {
+            const int t = q * 32 + lane;
+            if (t < nt) {
+                const int64_t o = t + (int64_t)nt * v;
+                float out = acc[q];
+                if (b) out -= b[o];
+                if (write_y) y[o] = out;
+                sq += (double)out * (double)out;
+            }
+        }
+    }
+    const double tot = block_sum_f64(sq, red);
+    if (threadIdx.x == 0 && partial) partial[blockIdx.x] = tot;
+}
+
+// Lane j of the warp ends with Σ over lanes of x[j] (31 shuffles for 32 sums).
+__device__ __forceinline__ float transpose_reduce32(float (&x)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = upper ? x[i] : x[i + s];
+            const float keep = upper ? x[i + s] : x[i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return x[0];
+}
+
+// g[f] += val_k <D[:,a_k], r[:,v_k]> for every nonzero (g zeroed by the caller).
+template <int NTW, bool SMEM_D, class VT>
+__global__ void __launch_bounds__(SIMT_THREADS)
+wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
+               const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D, int nt,
+               int na, int nv, const float* __restrict__ r, float* __restrict__ g, const life_sbb_state* gate,
+               int gate_mode) {
+    extern __shared__ float Ds[];
+    if (gate_skip(gate, gate_mode)) return;
+    constexpr int NTP = NTW * 32;
+    if (SMEM_D) {
+        stage_D<NTW>(Ds, D, nt, na);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+        const int beg = vox_ptr[v], end = vox_ptr[v + 1];
+        if (beg == end) continue;
+        float rr[NTW];
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) {
+            const int t = q * 32 + lane;
+            rr[q] = t < nt ? r[t + (int64_t)nt * v] : 0.0f;
+        }
+        for (int base = beg; base < end; base += 32) {
+            const int k = base + lane;
+            int a_l = 0;
+            if (k < end) a_l = atom[k];
+            float part[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int a = __shfl_sync(0xffffffffu, a_l, j);
+                float p = 0.0f;
+                if (SMEM_D) {
+                    const float* d = Ds + a * NTP + lane;
+#pragma unroll
+                    for (int q = 0; q < NTW; ++q) p = fmaf(d[q * 32], rr[q], p);
+                } else {
+                    const float* d = D + (int64_t)nt * a;
+#pragma unroll
+                    for (int q = 0; q < NTW; ++q) {
+                        const int t = q * 32 + lane;
+                        p = fmaf(t < nt ? __ldg(d + t) : 0.0f, rr[q], p);
+                    }
+                }
+                part[j] = p;
+            }
+            const float dot = transpose_reduce32(part, lane);
+            if (k < end) atomicAdd(g + fasc[k], ldval<VT>(val, k) * dot);
+        }
+    }
+}
+
+// dL/dD on the atom-sorted chunks: partial[c][θ] = Σ_{k∈c} val_k w[f_k] gy[θ, v_k].
+template <int NTW>
+__global__ void graddD_chunk_kernel(const int32_t* __restrict__ chunk_beg, int n_chunks,
+                                    const int32_t* __restrict__ voxel, const int32_t* __restrict__ fasc,
+                                    const float* __restrict__ val, const float* __restrict__ w,
+                                    const float* __restrict__ gy, int nt, float* __restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
+        float acc[NTW];
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) acc[q] = 0.0f;
+        const int beg = chunk_beg[c], end = chunk_beg[c + 1];
+        for (int k = beg; k < end; ++k) {
+            const float s = val[k] * w[fasc[k]];
+            if (s == 0.0f) continue;
+            const float* e = gy + (int64_t)nt * voxel[k];
+#pragma unroll
+            for (int q = 0; q < NTW; ++q) {
+                const int t = q * 32 + lane;
+                if (t < nt) acc[q] = fmaf(e[t], s, acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) {
+            const int t = q * 32 + lane;
+            if (t < nt) partial[(int64_t)c * nt + t] = acc[q];
+        }
+    }
+}
+
+__global__ void graddD_reduce_kernel(const int32_t* __restrict__ atom_chunk, int na, int nt,
+                                     const float* __restrict__ partial, float* __restrict__ gD) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)na * nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i / nt), t = (int)(i - (int64_t)a * nt);
+        float s = 0.0f;
+        for (int c = atom_chunk[a]; c < atom_chunk[a + 1]; ++c) s += partial[(int64_t)c * nt + t];
+        gD[i] = s;
+    }
+}
+
+// ----------------------------------------------------------- dispatchers
+
+#define LIFE_NTW_SWITCH(ntw, ...)                              \
+    switch (ntw) {                                             \
+        case 1: { constexpr int NTW = 1; __VA_ARGS__; } break; \
+        case 2: { constexpr int NTW = 2; __VA_ARGS__; } break; \
+        case 3: { constexpr int NTW = 3; __VA_ARGS__; } break; \
+        case 4: { constexpr int NTW = 4; __VA_ARGS__; } break; \
+        case 5: { constexpr int NTW = 5; __VA_ARGS__; } break; \
+        case 6: { constexpr int NTW = 6; __VA_ARGS__; } break; \
+        case 7: { constexpr int NTW = 7; __VA_ARGS__; } break; \
+        case 8: { constexpr int NTW = 8; __VA_ARGS__; } break; \
+        default: set_error("Ntheta > 256 is not supported"); return LIFE_ENOTSUP; \
+    }
+
+template <int NTW, bool SMEM, class VT>
+static life_status launch_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
+                              double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
+                              cudaStream_t s) {
+    const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
+    auto kern = dsc_simt_kernel<NTW, SMEM, VT>;
+    if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = ix->num_sms;
+    kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
+                                          ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p), D,
+                                          ix->nt, ix->na, ix->nv, w, b, y, partial, gate, gate_mode);
+    LIFE_CHECK_LAUNCH();
+    if (n_partial) *n_partial = grid;
+    return LIFE_OK;
+}
+
+template <int NTW, bool SMEM, class VT>
+static life_status launch_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                             int gate_mode, cudaStream_t s) {
+    const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
+    auto kern = wc_simt_kernel<NTW, SMEM, VT>;
+    if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<ix->num_sms, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
+                                                 ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p),
+                                                 D, ix->nt, ix->na, ix->nv, r, g, gate, gate_mode);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
+    const int ntw = (ix->nt + 31) / 32;
+    const bool smem = (size_t)ix->na * ntw * 32 * sizeof(float) <= SIMT_SMEM_LIMIT;
+    const bool bf = ix->precision == LIFE_BF16;
+    LIFE_NTW_SWITCH(ntw, {
+        if (smem && bf) return launch_dsc<NTW, true, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+        if (smem) return launch_dsc<NTW, true, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+        if (bf) return launch_dsc<NTW, false, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+        return launch_dsc<NTW, false, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+    });
+    return LIFE_OK;
+}
+
+life_status wc_simt(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                    int gate_mode, cudaStream_t s) {
+    const int ntw = (ix->nt + 31) / 32;
+    const bool smem = (size_t)ix->na * ntw * 32 * sizeof(float) <= SIMT_SMEM_LIMIT;
+    const bool bf = ix->precision == LIFE_BF16;
+    LIFE_NTW_SWITCH(ntw, {
+        if (smem && bf) return launch_wc<NTW, true, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s);
+        if (smem) return launch_wc<NTW, true, float>(ix, D, r, g, gate, gate_mode, s);
+        if (bf) return launch_wc<NTW, false, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s);
+        return launch_wc<NTW, false, float>(ix, D, r, g, gate, gate_mode, s);
+    });
+    return LIFE_OK;
+}
+
+life_status grad_D_simt(life_index_s* ix, const float* gy, const float* w, float* gD, cudaStream_t s) {
+    LIFE_TRY(build_atom_layout(ix, s));
+    AtomLayout& A = ix->atoml;
+    const int ntw = (ix->nt + 31) / 32;
+    TmpBuf partial;
+    LIFE_TRY(partial.alloc(sizeof(float) * (size_t)(A.n_chunks > 0 ? A.n_chunks : 1) * ix->nt, s));
+    if (A.n_chunks > 0) {
+        const int threads = 256;
+        int64_t blocks = ((int64_t)A.n_chunks * 32 + threads - 1) / threads;
+        if (blocks > (int64_t)ix->num_sms * 16) blocks = (int64_t)ix->num_sms * 16;
+        LIFE_NTW_SWITCH(ntw, {
+            graddD_chunk_kernel<NTW><<<(unsigned)blocks, threads, 0, s>>>(
+                A.chunk_beg.as<int32_t>(), A.n_chunks, A.voxel.as<int32_t>(), A.fasc.as<int32_t>(),
+                A.val.as<float>(), w, gy, ix->nt, partial.as<float>());
+        });
+        LIFE_CHECK_LAUNCH();
+    }
+    const int64_t n = (int64_t)ix->na * ix->nt;
+    graddD_reduce_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        A.atom_chunk.as<int32_t>(), ix->na, ix->nt, partial.as<float>(), gD);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+}  // namespace life

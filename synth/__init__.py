@@ -134,8 +134,9 @@ def make_problem(name: str = "custom", *, seed: int, n_theta: int = 96, n_atoms:
     vox = np.empty(n_raw, np.int32)
     fas = np.empty(n_raw, np.int32)
     val = np.empty(n_raw, np.float32)
+    u_c = np.ascontiguousarray(u)  # kept alive across the C call
     lib.synth_walks(seed, n_fasc, _ptr(lens), _ptr(off), nx, ny, nz, _ptr(vox_id), 1 if mask else 0,
-                    n_atoms, _ptr(np.ascontiguousarray(u)), persist, float(step_len[0]), float(step_len[1]),
+                    n_atoms, _ptr(u_c), persist, float(step_len[0]), float(step_len[1]),
                     _ptr(atom), _ptr(vox), _ptr(fas), _ptr(val))
     w_true = np.empty(n_fasc, np.float32)
     lib.synth_w_true(seed, n_fasc, zero_frac, _ptr(w_true))

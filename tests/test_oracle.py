@@ -164,6 +164,24 @@ def test_spmv_adjoint_linearity_demean():
     assert np.abs(col).max() <= 1e-12 * max(1.0, np.abs(y1).max())
 
 
+def test_wrapper_converts_inputs_safely():
+    # float32 inputs are converted to float64 copies; those copies must stay alive
+    # for the whole C call (a dangling copy once corrupted results)
+    p = synth.config_problem("tiny")
+    D, _ = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    D32 = D.astype(np.float32)
+    w32 = np.random.default_rng(0).random(p.n_fasc).astype(np.float32)
+    r32 = np.random.default_rng(1).standard_normal(p.n_theta * p.n_voxels).astype(np.float32)
+    for _ in range(3):
+        y1 = oracle.dsc(phi, D32, w32, p.n_theta, p.n_voxels)
+        y2 = oracle.dsc(phi, D32.astype(np.float64), w32.astype(np.float64), p.n_theta, p.n_voxels)
+        np.testing.assert_array_equal(y1, y2)
+        g1 = oracle.wc(phi, D32, r32, p.n_theta, p.n_fasc)
+        g2 = oracle.wc(phi, D32.astype(np.float64), r32.astype(np.float64), p.n_theta, p.n_fasc)
+        np.testing.assert_array_equal(g1, g2)
+
+
 def test_spmv_single_nonzero():
     nt, na, nv, nf = 5, 4, 3, 2
     D = np.arange(1.0, nt * na + 1.0)
