@@ -1,0 +1,429 @@
+"""LiFE SBB-NNLS throughput on one or more GB300s (one process per GPU, replicas).
+
+A step is one SBB-NNLS iteration (Eq. 5-8, Algorithm 1: DSC with the residual,
+WC, the projected gradient, DSC of the projected gradient, WC on Eq. 8
+iterations, the BB step and the projection) on the paper-scale synthetic
+problem: Nθ = 96, Na = 360, a 96x96x72 grid with an ellipsoidal mask, Nf = 500k
+persistent-walk fascicles of 20-300 steps.  ``value`` is whole-job SBB iterations
+per second (every rank runs its own replica; max-over-ranks time).
+
+Default run (no flags): 1 GPU, the fastest path beside the plain FP32 path,
+20 timed steps after 5 warm-up steps.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DSC+WC effective HBM GB/s (% of peak) and SBB-NNLS iters/s at Nf=500k, vs plain FP32"
+UNIT = "iter/s"
+PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return PEAK_FALLBACK, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ workload
+
+def make_workload(name: str):
+    import synth
+    t0 = time.time()
+    p = synth.config_problem(name)
+    return p, time.time() - t0
+
+
+def workload_desc(p, nnz):
+    mask = "ellipsoidal mask" if p.meta.get("mask") else "no mask"
+    gx, gy, gz = p.grid
+    return (f"paper-scale LiFE: Ntheta={p.n_theta}, Na={p.n_atoms}, {gx}x{gy}x{gz} grid with {mask} "
+            f"(Nv={p.n_voxels}), Nf={p.n_fasc} persistent walks of {p.meta['steps'][0]}-{p.meta['steps'][1]} "
+            f"steps, nnz={nnz} after merging {p.n_raw} raw entries")
+
+
+# ------------------------------------------------------------ GPU arm
+
+class GpuPath:
+    """Index + device buffers for one precision/algorithm choice."""
+
+    def __init__(self, life, p, D, b, precision, algo):
+        import torch
+        self.life = life
+        t0 = time.time()
+        self.idx = life.upload_problem(p, precision=precision, algo=algo)
+        torch.cuda.synchronize()
+        self.build_s = time.time() - t0
+        self.info = self.idx.info()
+        self.p, self.D, self.b = p, D, b
+        self.w = torch.ones(p.n_fasc, dtype=torch.float32, device="cuda")
+        self.st = life.new_sbb_state()
+        self.ws = life.new_sbb_workspace(self.idx)
+
+    def reset(self):
+        self.w.fill_(1.0)
+        self.life.life_sbb_state_init(self.st)
+
+    def run_steps(self, k):
+        self.life.life_sbbnnls_solve(self.idx, self.D, self.b, self.w, k, self.st, self.ws)
+
+
+def time_steps(path, steps, warmup):
+    import torch
+    path.reset()
+    path.run_steps(warmup)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    path.run_steps(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_kernel(fn, reps=10):
+    """Average device time of fn() over reps launches, CUDA events on the current stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def spmv_bytes(path, kind, fused_b=False):
+    """Algorithmic bytes of one SpMV call: the canonical compact Phi stream
+    (u16 atom + i32 fascicle + value: 10 B/nonzero FP32, 8 B BF16) plus the CSR
+    pointers, the dense vectors read and written, and D once."""
+    p, info = path.p, path.info
+    nnz = info["nnz"]
+    per_nz = 8 if info["precision"] == 1 else 10
+    sig = 4 * p.n_theta * p.n_voxels
+    phi = per_nz * nnz + 4 * (p.n_voxels + 1)
+    dbytes = 4 * p.n_theta * p.n_atoms
+    if kind == "dsc":
+        return phi + 4 * p.n_fasc + sig + (sig if fused_b else 0) + dbytes
+    return phi + sig + 4 * p.n_fasc + dbytes
+
+
+def measure_kernels(life, path):
+    import torch
+    p = path.p
+    r = path.b
+    g = torch.empty(p.n_fasc, dtype=torch.float32, device="cuda")
+    e = torch.empty(p.n_theta * p.n_voxels, dtype=torch.float32, device="cuda")
+    w = torch.rand(p.n_fasc, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    t_dsc = time_kernel(lambda: life.life_dsc(path.idx, path.D, w, b=path.b, y=e))
+    t_wc = time_kernel(lambda: life.life_wc(path.idx, path.D, r, g=g))
+    b_dsc = spmv_bytes(path, "dsc", fused_b=True)
+    b_wc = spmv_bytes(path, "wc")
+    return dict(dsc_s=t_dsc, wc_s=t_wc, dsc_bytes=b_dsc, wc_bytes=b_wc)
+
+
+def e2e_steps(life, path, steps, warmup):
+    """Per step through the public API with host buffers: w (pinned host) -> device,
+    one SBB iteration, w and the state -> host."""
+    import torch
+    p = path.p
+    w_host = torch.ones(p.n_fasc, dtype=torch.float32).pin_memory()
+    st_host = torch.empty(path.st.numel(), dtype=torch.uint8).pin_memory()
+    s = torch.cuda.current_stream()
+    path.reset()
+
+    def one():
+        path.w.copy_(w_host, non_blocking=True)
+        life.life_sbbnnls_step(path.idx, path.D, path.b, path.w, path.st, path.ws)
+        w_host.copy_(path.w, non_blocking=True)
+        st_host.copy_(path.st, non_blocking=True)
+        s.synchronize()
+
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t0
+    return steps / dt, 4 * p.n_fasc, 4 * p.n_fasc + path.st.numel()
+
+
+def launches_per_step(path):
+    # DSC + WC + project + scalars + DSC + WC + sumsq + scalars + update
+    return 9
+
+
+def cpu_sample_baseline(p, D32, b, frac_voxels=0.15, reps=3):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample: one SBB
+    iteration on the sub-problem of the first `frac_voxels` of the voxels."""
+    import numpy as np
+    import oracle
+    nv_s = max(1, int(p.n_voxels * frac_voxels))
+    sel = p.coo_voxel < nv_s
+    phi = oracle.Phi(p.coo_atom[sel], p.coo_voxel[sel], p.coo_fasc[sel], p.coo_val[sel])
+    b_s = np.asarray(b[: p.n_theta * nv_s], np.float64)
+    best = None
+    for _ in range(reps):
+        w = np.ones(p.n_fasc)
+        t0 = time.perf_counter()
+        oracle.sbb_step(phi, D32, b_s, w, p.n_theta, nv_s, p.n_fasc, oracle.SbbState())
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    frac_nnz = len(phi) / p.n_raw
+    return dict(iter_s=best, frac=frac_nnz, nnz_sample=len(phi), nv_sample=nv_s)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1905_06234_gb300 as life
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    life.load()
+    peaks, peak_src = read_peaks()
+    p, gen_s = make_workload(args.workload)
+    dev = torch.device("cuda", local)
+    g = torch.from_numpy(p.grad_dirs)
+    u = torch.from_numpy(p.atom_dirs)
+    D, _ = life.life_dictionary(g, u, p.bval, p.lam)
+    # the measured signal b = M w_true + noise, computed on the device
+    fp32 = GpuPath(life, p, D, torch.zeros(p.n_theta * p.n_voxels, device=dev), life.LIFE_FP32, life.LIFE_ALGO_SIMT)
+    w_true = torch.from_numpy(p.w_true).to(dev)
+    b, _ = life.life_dsc(fp32.idx, D, w_true)
+    b += torch.from_numpy(p.noise).to(dev)
+    fp32.b = b
+    paths = {"fp32-simt": fp32}
+    if args.precision in ("bf16", "both"):
+        try:
+            paths["bf16-tc"] = GpuPath(life, p, D, b, life.LIFE_BF16, life.LIFE_ALGO_TC)
+        except life.LifeError as e:
+            paths["bf16-tc"] = None
+            if rank == 0:
+                print(f"# bf16 tensor-core path unavailable: {e}", file=sys.stderr)
+    if args.profile:
+        # Profiling mode: only the SBB steps of each path run between
+        # cudaProfilerStart/Stop (for ncu --profile-from-start off).
+        for name, path in paths.items():
+            if path is None:
+                continue
+            path.reset()
+            path.run_steps(args.warmup)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            path.run_steps(args.steps)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        if dist:
+            dist.destroy_process_group()
+        return
+    results = {}
+    for name, path in paths.items():
+        if path is None:
+            continue
+        kern = measure_kernels(life, path)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        dt = time_steps(path, args.steps, args.warmup)
+        ck = clocks.stop()
+        if dist:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t)
+        results[name] = dict(path=path, dt=dt, kern=kern, clocks=ck)
+    best_name = min(results, key=lambda k: results[k]["dt"])
+    best = results[best_name]
+    path = best["path"]
+    e2e_val, h2d, d2h = e2e_steps(life, path, max(3, args.steps // 2), 2)
+    st = life.read_sbb_state(path.st)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    kern = best["kern"]
+    # dominant kernel of an iteration: 2 DSC + 1.5 WC per iteration on average (Sec. 2.2)
+    share_dsc, share_wc = 2 * kern["dsc_s"], 1.5 * kern["wc_s"]
+    dom = "dsc" if share_dsc >= share_wc else "wc"
+    t_dom = kern[f"{dom}_s"]
+    achieved = kern[f"{dom}_bytes"] / t_dom / 1e9
+    peak = float(peaks.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"]))
+    dsc_wc_gbs = (kern["dsc_bytes"] + kern["wc_bytes"]) / (kern["dsc_s"] + kern["wc_s"]) / 1e9
+    cpu = cpu_sample_baseline(p, D.cpu().numpy(), b.cpu().numpy())
+    cpu_value = cpu["frac"] / cpu["iter_s"]
+    value = world * args.steps / best["dt"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": best["dt"] / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if best_name.startswith("bf16") else "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(p, path.info["nnz"]), "path": best_name,
+                   "l2": "inputs larger than L2 (Phi stream %.2f GB per SpMV)" % (path.info["stream_bytes"] / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs", "traffic": None},
+        "dsc_wc": {"gbs": dsc_wc_gbs, "frac_of_peak": dsc_wc_gbs / peak, "dsc_ms": kern["dsc_s"] * 1e3,
+                   "wc_ms": kern["wc_s"] * 1e3},
+        "paths": {k: {"iter_per_s": args.steps / v["dt"], "dsc_ms": v["kern"]["dsc_s"] * 1e3,
+                      "wc_ms": v["kern"]["wc_s"] * 1e3,
+                      "dsc_gbs": v["kern"]["dsc_bytes"] / v["kern"]["dsc_s"] / 1e9,
+                      "wc_gbs": v["kern"]["wc_bytes"] / v["kern"]["wc_s"] / 1e9,
+                      "index_build_s": v["path"].build_s} for k, v in results.items()},
+        "vs_plain_fp32": (args.steps / best["dt"]) / (args.steps / results["fp32-simt"]["dt"]),
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one FP64 SBB iteration on the voxels 0..%d sub-problem (%d of %d raw entries), "
+                                   "scaled by the entry fraction" % (cpu["nv_sample"], cpu["nnz_sample"], p.n_raw)},
+        "e2e": {"value": e2e_val * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step(path) * (args.steps) * world,
+        "clocks": best["clocks"],
+        "final_state": {"it": st["it"], "obj": st["obj"], "alpha": st["alpha"]},
+        "gen_s": gen_s,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    p, _ = make_workload(args.workload)
+    D64, _ = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)
+    D32 = D64.astype(np.float32)
+    frac_v = 0.02
+    nv_s = max(1, int(p.n_voxels * frac_v))
+    sel = p.coo_voxel < nv_s
+    phi = oracle.Phi(p.coo_atom[sel], p.coo_voxel[sel], p.coo_fasc[sel], p.coo_val[sel])
+    b = oracle.problem_signal(phi, D32, p.w_true, p.noise[: p.n_theta * nv_s], p.n_theta, nv_s)
+    w = np.ones(p.n_fasc)
+    st = oracle.SbbState()
+    for _ in range(args.warmup):
+        oracle.sbb_step(phi, D32, b, w, p.n_theta, nv_s, p.n_fasc, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sbb_step(phi, D32, b, w, p.n_theta, nv_s, p.n_fasc, st)
+    dt = time.perf_counter() - t0
+    frac = len(phi) / p.n_raw
+    value = frac * args.steps / dt
+    sample = ("FP64 SBB iterations on the voxels 0..%d sub-problem (%d of %d raw entries), "
+              "throughput scaled by the entry fraction" % (nv_s, len(phi), p.n_raw))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 / frac,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(p, None), "path": "oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="paper", choices=["paper", "medium", "tiny"])
+    ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
+    ap.add_argument("--profile", action="store_true",
+                    help="run only warm-up + timed SBB steps inside cudaProfilerStart/Stop, print nothing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
