@@ -150,6 +150,28 @@ LIFE_API life_status life_wc(life_index idx, const float* D, const float* r, flo
 LIFE_API life_status life_dsc_grad_D(life_index idx, const float* gy, const float* w, float* gD, void* stream);
 
 /*
+ * The same dL/dD as life_dsc_grad_D, for callers that may not allocate device
+ * memory while they run: code being captured into a CUDA graph, where cudaMalloc
+ * is not allowed, or a real-time loop that allocates only at start-up.
+ * life_dsc_grad_D allocates temporary memory on every call for its split-K
+ * partial sums; this entry point allocates nothing and keeps those sums in a
+ * fixed device array compiled into the library instead.  The paper has no
+ * counterpart to this call.
+ *  - Limit: (number of atom chunks) x Nθ <= 2^20 floats (the array is 4 MiB, held
+ *    on every GPU that loads the library until the process exits); a larger index
+ *    gets LIFE_ERANGE.  An atom chunk is at most 256 nonzeros of one atom.
+ *  - Prerequisite: the atom-sorted layout, which the first life_dsc_grad_D call
+ *    on the index builds; without it the call returns LIFE_EINVAL.
+ *  - Set-up: the first call on each device looks up the array's device address
+ *    with that device current; make that first call before any stream capture.
+ *  - Every call shares the one array, so calls that overlap on the GPU race.
+ *    Nothing in it needs clearing: each slot a call reads was written earlier in
+ *    the same call.
+ */
+LIFE_API life_status life_dsc_grad_D_noalloc(life_index idx, const float* gy, const float* w, float* gD,
+                                             void* stream);
+
+/*
  * Dictionary of canonical diffusion atoms (the D of Eq. 3) for the exponential
  * atom model D_raw[θ,a] = exp(-bval·lam·(g_θ·u_a)^2), each column demeaned over θ,
  * and its derivative dD/dlam (also demeaned).  Computed in double precision,

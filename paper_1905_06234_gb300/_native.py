@@ -25,7 +25,7 @@ _STATUS_NAMES = {0: "LIFE_OK", 1: "LIFE_EINVAL", 2: "LIFE_ERANGE", 3: "LIFE_ENOM
 EXPORTS = [
     "life_build_index", "life_index_free", "life_index_get_info", "life_index_export",
     "life_index_export_voxel_streams", "life_dsc", "life_wc",
-    "life_dsc_grad_D", "life_dictionary", "life_dot_f32", "life_sbb_workspace_bytes", "life_sbb_state_init",
+    "life_dsc_grad_D", "life_dsc_grad_D_noalloc", "life_dictionary", "life_dot_f32", "life_sbb_workspace_bytes", "life_sbb_state_init",
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_check_device_status", "life_last_error", "life_version",
 ]
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False):
     L.life_dsc.argtypes = [P, P, P, P, P, P, P]
     L.life_wc.argtypes = [P, P, P, P, P, P]
     L.life_dsc_grad_D.argtypes = [P, P, P, P, P]
+    L.life_dsc_grad_D_noalloc.argtypes = [P, P, P, P, P]
     L.life_dictionary.argtypes = [i32, i32, P, P, dbl, dbl, P, P, P]
     L.life_dot_f32.argtypes = [i64, P, P, P, P]
     L.life_sbb_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
@@ -245,6 +246,15 @@ def life_dsc_grad_D(index: LifeIndex, gy, w, gD=None):
     if gD is None:
         gD = torch.empty(index.n_theta * index.n_atoms, dtype=torch.float32, device=w.device)
     _check(load().life_dsc_grad_D(index.handle, _ptr(gy), _ptr(w), _ptr(gD), _stream()))
+    return gD
+
+
+def life_dsc_grad_D_noalloc(index: LifeIndex, gy, w, gD):
+    """dL/dD into the caller's gD with no device allocation (see include/life.h)."""
+    _need(gy, torch.float32, index.n_theta * index.n_voxels, "gy")
+    _need(w, torch.float32, index.n_fasc, "w")
+    _need(gD, torch.float32, index.n_theta * index.n_atoms, "gD")
+    _check(load().life_dsc_grad_D_noalloc(index.handle, _ptr(gy), _ptr(w), _ptr(gD), _stream()))
     return gD
 
 

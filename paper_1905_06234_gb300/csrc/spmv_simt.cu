@@ -325,3 +325,88 @@ life_status grad_D_simt(life_index_s* ix, const float* gy, const float* w, float
 }
 
 }  // namespace life
+
+// ------------------------------------------- dL/dD without device allocation
+//
+// life_dsc_grad_D_noalloc: the same two kernels as life_dsc_grad_D, with the
+// split-K partial sums in a fixed device array compiled into this library
+// instead of memory allocated per call.  It serves callers that may not
+// allocate device memory while they run (for example code being captured into a
+// CUDA graph, or an allocation-free real-time loop).
+
+#include <mutex>
+
+namespace life {
+
+constexpr int64_t GRAD_D_NOALLOC_MAX_FLOATS = int64_t(1) << 20;  // 4 MiB on every device
+
+// Device array for the partial sums.  In host code this name is only a stand-in;
+// its device address comes from cudaGetSymbolAddress (see noalloc_scratch()).
+static __device__ __align__(256) float g_grad_d_scratch[GRAD_D_NOALLOC_MAX_FLOATS];
+
+// Per-device address of g_grad_d_scratch, looked up once with that device current.
+static life_status noalloc_scratch(float** out) {
+    static std::mutex mu;
+    static float* addr[64] = {nullptr};
+    int dev = 0;
+    LIFE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("life_dsc_grad_D_noalloc: device ordinal %d out of range", dev);
+        return LIFE_ERANGE;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_grad_d_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("life_dsc_grad_D_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return LIFE_ECUDA;
+        }
+        addr[dev] = static_cast<float*>(p);
+    }
+    *out = addr[dev];
+    return LIFE_OK;
+}
+
+}  // namespace life
+
+extern "C" life_status life_dsc_grad_D_noalloc(life_index idx, const float* gy, const float* w, float* gD,
+                                               void* stream) {
+    using namespace life;
+    if (!idx || !gy || !w || !gD) {
+        set_error("life_dsc_grad_D_noalloc: null argument");
+        return LIFE_EINVAL;
+    }
+    AtomLayout& A = idx->atoml;
+    if (!A.built) {
+        set_error("life_dsc_grad_D_noalloc: the atom-sorted layout is missing; call life_dsc_grad_D once "
+                  "on this index during set-up (that call builds it)");
+        return LIFE_EINVAL;
+    }
+    const int64_t need = (int64_t)A.n_chunks * idx->nt;
+    if (need > GRAD_D_NOALLOC_MAX_FLOATS) {
+        set_error("life_dsc_grad_D_noalloc: needs %lld floats of scratch (atom chunks x Ntheta), the fixed "
+                  "array holds %lld; use life_dsc_grad_D", (long long)need, (long long)GRAD_D_NOALLOC_MAX_FLOATS);
+        return LIFE_ERANGE;
+    }
+    float* partial = nullptr;
+    LIFE_TRY(noalloc_scratch(&partial));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ntw = (idx->nt + 31) / 32;
+    if (A.n_chunks > 0) {
+        const int threads = 256;
+        int64_t blocks = ((int64_t)A.n_chunks * 32 + threads - 1) / threads;
+        if (blocks > (int64_t)idx->num_sms * 16) blocks = (int64_t)idx->num_sms * 16;
+        LIFE_NTW_SWITCH(ntw, {
+            graddD_chunk_kernel<NTW><<<(unsigned)blocks, threads, 0, s>>>(
+                A.chunk_beg.as<int32_t>(), A.n_chunks, A.voxel.as<int32_t>(), A.fasc.as<int32_t>(),
+                A.val.as<float>(), w, gy, idx->nt, partial);
+        });
+        LIFE_CHECK_LAUNCH();
+    }
+    const int64_t n = (int64_t)idx->na * idx->nt;
+    graddD_reduce_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        A.atom_chunk.as<int32_t>(), idx->na, idx->nt, partial, gD);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
