@@ -69,6 +69,9 @@ typedef struct {
     int64_t n_bricks;      /* TC path: locality bricks; 0 otherwise */
     int64_t device_bytes;  /* device memory held by the index */
     int64_t stream_bytes;  /* bytes of Phi one SpMV streams from memory */
+    int64_t n_brick_fasc;  /* TC path: total entries of the brick-local fascicle tables */
+    int32_t n_sub;         /* TC path: 32-atom sub-chunks per tile */
+    int32_t brick_edge;    /* TC path: spatial brick edge in voxels (0 = voxel-id groups) */
 } life_index_info;
 
 /*
@@ -117,6 +120,23 @@ LIFE_API life_status life_index_export(life_index idx, int32_t layout, int32_t* 
  */
 LIFE_API life_status life_index_export_voxel_streams(life_index idx, int32_t* vox_ptr, int32_t* atom,
                                                      int32_t* fasc, float* val, void* stream);
+
+/*
+ * Copies the tensor-core layout (TC path only; LIFE_ENOTSUP otherwise), for
+ * bit-exact tests of the restructuring.  Sizes come from life_index_get_info:
+ *  tile_vox [n_tiles·128]        voxel of each tile row, -1 for padding rows
+ *  sub_ptr [n_tiles·n_sub + 1]   entry offsets of each (tile, 32-atom sub-chunk)
+ *  brick_tile_ptr [n_bricks+1]   tiles of brick b: [ptr[b], ptr[b+1])
+ *  brick_fasc_ptr [n_bricks+1], brick_fasc [n_brick_fasc]  brick-local fascicle tables
+ *  brick_order [n_bricks]        processing order
+ *  va, fl [nnz] (uint16)         row | atom << 7;  brick-local fascicle | 0x8000 on run continuation
+ *  val [nnz]                     BF16 values widened to float32
+ * Device outputs; any may be NULL.  Synchronizes `stream`.
+ */
+LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* sub_ptr,
+                                             int32_t* brick_tile_ptr, int32_t* brick_fasc_ptr,
+                                             int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
+                                             uint16_t* fl, float* val, void* stream);
 
 /*
  * DSC, y = M w (Sec. 4 "DSC"; Eq. 1 with Eq. 3-4):

@@ -7,7 +7,7 @@ wrapper.  Build the library with ``python -m paper_1905_06234_gb300.build``.
 from ._native import (  # noqa: F401
     EXPORTS, LIFE_ALGO_AUTO, LIFE_ALGO_SIMT, LIFE_ALGO_TC, LIFE_BF16, LIFE_FP32, LIFE_LAYOUT_ATOM,
     LIFE_LAYOUT_FIBER, LIFE_LAYOUT_VOXEL, LifeError, LifeIndex, life_build_index, life_check_device_status,
-    life_dictionary, life_dot_f32, life_dsc, life_dsc_grad_D, life_dsc_grad_D_noalloc, life_index_export, life_index_export_voxel_streams, life_sbb_state_init,
+    life_dictionary, life_dot_f32, life_dsc, life_dsc_grad_D, life_dsc_grad_D_noalloc, life_index_export, life_index_export_tiles, life_index_export_voxel_streams, life_sbb_state_init,
     life_sbb_workspace_bytes, life_sbbnnls_solve, life_sbbnnls_step, life_version, life_wc, load, new_sbb_state,
     new_sbb_workspace, read_sbb_state,
 )

@@ -24,7 +24,7 @@ _STATUS_NAMES = {0: "LIFE_OK", 1: "LIFE_EINVAL", 2: "LIFE_ERANGE", 3: "LIFE_ENOM
 # Every symbol include/life.h declares (checked by the CPU test suite).
 EXPORTS = [
     "life_build_index", "life_index_free", "life_index_get_info", "life_index_export",
-    "life_index_export_voxel_streams", "life_dsc", "life_wc",
+    "life_index_export_voxel_streams", "life_index_export_tiles", "life_dsc", "life_wc",
     "life_dsc_grad_D", "life_dsc_grad_D_noalloc", "life_dictionary", "life_dot_f32", "life_sbb_workspace_bytes", "life_sbb_state_init",
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_check_device_status", "life_last_error", "life_version",
 ]
@@ -45,7 +45,8 @@ class life_index_info(ctypes.Structure):
     _fields_ = [("nnz_raw", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_theta", ctypes.c_int32),
                 ("n_atoms", ctypes.c_int32), ("n_voxels", ctypes.c_int32), ("n_fasc", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
-                ("n_bricks", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("stream_bytes", ctypes.c_int64)]
+                ("n_bricks", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("stream_bytes", ctypes.c_int64),
+                ("n_brick_fasc", ctypes.c_int64), ("n_sub", ctypes.c_int32), ("brick_edge", ctypes.c_int32)]
 
 
 class life_sbb_state(ctypes.Structure):
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = False):
     L.life_index_get_info.argtypes = [P, ctypes.POINTER(life_index_info)]
     L.life_index_export.argtypes = [P, i32, P, P, P, P, P]
     L.life_index_export_voxel_streams.argtypes = [P, P, P, P, P, P]
+    L.life_index_export_tiles.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
     L.life_dsc.argtypes = [P, P, P, P, P, P, P]
     L.life_wc.argtypes = [P, P, P, P, P, P]
     L.life_dsc_grad_D.argtypes = [P, P, P, P, P]
@@ -210,6 +212,26 @@ def life_index_export_voxel_streams(index: LifeIndex):
     x = torch.empty(m, dtype=torch.float32, device=dev)
     _check(load().life_index_export_voxel_streams(index.handle, _ptr(ptr), _ptr(a), _ptr(f), _ptr(x), _stream()))
     return ptr, a, f, x
+
+
+def life_index_export_tiles(index: LifeIndex) -> dict:
+    """The tensor-core layout arrays (see include/life.h), as device tensors."""
+    i = index.info()
+    dev = torch.device("cuda")
+    nt, nb, m = i["n_tiles"], i["n_bricks"], i["nnz"]
+    out = dict(tile_vox=torch.empty(nt * 128, dtype=torch.int32, device=dev),
+               sub_ptr=torch.empty(nt * i["n_sub"] + 1, dtype=torch.int32, device=dev),
+               brick_tile_ptr=torch.empty(nb + 1, dtype=torch.int32, device=dev),
+               brick_fasc_ptr=torch.empty(nb + 1, dtype=torch.int32, device=dev),
+               brick_fasc=torch.empty(max(i["n_brick_fasc"], 1), dtype=torch.int32, device=dev),
+               brick_order=torch.empty(max(nb, 1), dtype=torch.int32, device=dev),
+               va=torch.empty(max(m, 1), dtype=torch.int16, device=dev),
+               fl=torch.empty(max(m, 1), dtype=torch.int16, device=dev),
+               val=torch.empty(max(m, 1), dtype=torch.float32, device=dev))
+    _check(load().life_index_export_tiles(index.handle, *[_ptr(out[k]) for k in (
+        "tile_vox", "sub_ptr", "brick_tile_ptr", "brick_fasc_ptr", "brick_fasc", "brick_order", "va", "fl", "val")],
+        _stream()))
+    return out
 
 
 def life_dsc(index: LifeIndex, D, w, b=None, y=None, want_y=True, sumsq=False):

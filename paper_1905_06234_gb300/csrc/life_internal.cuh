@@ -99,7 +99,6 @@ struct TmpBuf {
 // ------------------------------------------------------------------ layouts
 
 constexpr int TILE_V = 128;        // voxels per tensor-core tile (MMA M)
-constexpr int KCHUNK = 64;         // atoms per K chunk of the tile layout
 constexpr int MAX_BRICK_FASC = 16384;  // brick-local fascicle table capacity (64 KB of FP32)
 constexpr int RED_SLOTS = 4096;    // per-call FP64 partial-sum slots
 
@@ -123,20 +122,26 @@ struct AtomLayout {
     int32_t n_chunks = 0;
 };
 
-// TC path: bricks of voxel tiles with brick-local fascicle numbering.
+// TC path: spatial bricks of 128-voxel tiles with brick-local fascicle numbering.
+// Entries are sorted by (tile, atom, row, fascicle); sub_ptr splits each tile
+// into 32-atom sub-chunks.
 struct TileLayout {
     bool built = false;
-    int64_t n_tiles = 0, n_bricks = 0, n_nnz = 0;   // n_nnz includes alignment padding
-    int32_t n_kchunks = 0;                           // ceil(Na / KCHUNK)
-    DevBuf tile_vox;        // int32 [n_tiles * TILE_V] voxel id per tile row (-1 = padding)
-    DevBuf tile_chunk_ptr;  // int32 [n_tiles * (n_kchunks+1)] nonzero offsets per (tile, chunk)
-    DevBuf brick_tile_ptr;  // int32 [n_bricks+1] tiles of each brick (consecutive)
-    DevBuf brick_fasc_ptr;  // int32 [n_bricks+1] offsets into brick_fasc
-    DevBuf brick_fasc;      // int32 [sum] global fascicle id of each brick-local fascicle
-    DevBuf brick_order;     // int32 [n_bricks] processing order (largest first)
-    DevBuf va;              // uint16 [n_nnz]: v_local | (a << 7)
-    DevBuf fl;              // uint16 [n_nnz]: brick-local fascicle
-    DevBuf val;             // bf16 [n_nnz]
+    int64_t n_tiles = 0, n_bricks = 0, n_nnz = 0;
+    int32_t np = 0;          // Nθ padded to a multiple of 16 (MMA N or K)
+    int32_t kp = 0;          // Na padded to a multiple of 64 (MMA K or N)
+    int32_t n_sub = 0;       // kp / 32
+    int32_t max_fb = 0;      // largest brick-local fascicle table
+    int32_t brick_edge = 0;  // spatial brick edge used (0 = voxel-id groups)
+    DevBuf tile_vox;         // int32 [n_tiles * TILE_V] voxel id per tile row (-1 = padding)
+    DevBuf sub_ptr;          // int32 [n_tiles * n_sub + 1] entry offsets per (tile, 32-atom sub-chunk)
+    DevBuf brick_tile_ptr;   // int32 [n_bricks + 1] tiles of each brick (consecutive)
+    DevBuf brick_fasc_ptr;   // int32 [n_bricks + 1] offsets into brick_fasc
+    DevBuf brick_fasc;       // int32 [sum] global fascicle id of each brick-local fascicle
+    DevBuf brick_order;      // int32 [n_bricks] bricks by decreasing entry count
+    DevBuf va;               // uint16 [n_nnz]: row | (atom << 7)
+    DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
+    DevBuf val;              // bf16 [n_nnz]
 };
 
 }  // namespace life
@@ -169,6 +174,9 @@ life_status build_voxel_layout(life_index_s* ix, const int32_t* atom, const int3
                                const int32_t* fasc, const float* val, cudaStream_t s);
 life_status build_atom_layout(life_index_s* ix, cudaStream_t s);
 life_status build_tile_layout(life_index_s* ix, cudaStream_t s);
+life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, int32_t* brick_tile_ptr,
+                         int32_t* brick_fasc_ptr, int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
+                         uint16_t* fl, float* val, cudaStream_t s);
 life_status export_voxel_streams(life_index_s* ix, int32_t* vox_ptr, int32_t* atom, int32_t* fasc,
                                  float* val, cudaStream_t s);
 life_status export_layout(life_index_s* ix, int layout, int32_t* atom, int32_t* voxel, int32_t* fasc,

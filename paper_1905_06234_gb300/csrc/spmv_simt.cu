@@ -101,6 +101,7 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
                 }
             }
         }
+        float sqv = 0.0f;  // this voxel's Σ out² in FP32, promoted to FP64 once per voxel
 #pragma unroll
         for (int q = 0; q < NTW; ++q) {
             const int t = q * 32 + lane;
@@ -109,9 +110,12 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
                 float out = acc[q];
                 if (b) out -= b[o];
                 if (write_y) y[o] = out;
-                sq += (double)out * (double)out;
+                sqv = fmaf(out, out, sqv);
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sqv += __shfl_xor_sync(0xffffffffu, sqv, o);
+        if (lane == 0) sq += (double)sqv;
     }
     const double tot = block_sum_f64(sq, red);
     if (threadIdx.x == 0 && partial) partial[blockIdx.x] = tot;

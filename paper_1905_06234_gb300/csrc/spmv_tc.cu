@@ -1,23 +1,1117 @@
-// Tensor-core (tcgen05) SpMVs on the brick/tile layout.
+// Tensor-core (tcgen05) SpMVs on the brick/tile layout, BF16 storage.
+//
+// Both SpMVs are split into a sparse part and a dense contraction with the
+// dictionary (Eq. 3: M_v = D Phi_v):
+//   DSC  y[:,v] = D · S[:,v],   S[a,v] = Σ_f val·w[f]        (S built in shared memory)
+//   WC   Z[a,v] = (Dᵀ r[:,v])[a],  g[f] += val·Z[a,v]         (Z read back from TMEM)
+// One CTA per SM walks spatial bricks of voxels (largest first, snake order).
+// A brick's fascicles are renumbered locally so that w is gathered, and g is
+// accumulated, in shared memory: each global gather or atomic then serves all of
+// a fascicle's entries inside the brick instead of one entry.
+//
+// The dense contraction runs on tcgen05.mma (kind::f16: BF16 operands, FP32
+// accumulation in TMEM), one 128-voxel tile at a time (MMA M = 128).  Operands
+// are K-major, no-swizzle core-matrix layouts in shared memory.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
 #include "life_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace life {
 
+using namespace ptx;
+
+constexpr int SUB = 32;                  // atoms per sub-chunk (offset granularity)
+constexpr uint16_t CONT = 0x8000;        // entry continues the previous entry's (atom, row)
+constexpr uint32_t WAIT_LIMIT = 1u << 24; // polls before a wait gives up (about a second)
+constexpr int ZSTRIDE = 33;              // padded row stride (floats) of the Z staging buffer
+
+static int nbits64(int64_t n) {
+    if (n <= 1) return 0;
+    uint64_t x = (uint64_t)(n - 1);
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+static unsigned grid1d(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)device_sm_count() * 32;
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ============================================================ layout build
+
+// key = tile | atom | row | fascicle  (payload: position in the merged list)
+__global__ void tile_key_kernel(const uint64_t* __restrict__ ukey, int64_t m, int sa, int sv, uint64_t amask,
+                                uint64_t fmask, int bf, const int32_t* __restrict__ vox_tile,
+                                const int32_t* __restrict__ vox_row, uint64_t* __restrict__ key,
+                                uint32_t* __restrict__ pay) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ukey[i];
+        const uint64_t v = k >> sv, a = (k >> sa) & amask, f = k & fmask;
+        const uint64_t t = (uint64_t)vox_tile[v], row = (uint64_t)vox_row[v];
+        key[i] = (t << (16 + bf)) | (a << (7 + bf)) | (row << bf) | f;
+        pay[i] = (uint32_t)i;
+    }
+}
+
+// key2 = brick | fascicle (payload: position in tile order)
+__global__ void brick_key_kernel(const uint64_t* __restrict__ skey, int64_t m, int bf,
+                                 const int32_t* __restrict__ tile_brick, uint64_t* __restrict__ key2,
+                                 uint32_t* __restrict__ pay2) {
+    const uint64_t fmask = (1ull << bf) - 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = skey[j];
+        const uint64_t t = k >> (16 + bf);
+        key2[j] = ((uint64_t)tile_brick[t] << bf) | (k & fmask);
+        pay2[j] = (uint32_t)j;
+    }
+}
+
+__global__ void head_flag_kernel(const uint64_t* __restrict__ key, int64_t m, int32_t* __restrict__ head) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        head[j] = (j == 0 || key[j] != key[j - 1]) ? 1 : 0;
+}
+
+// Distinct fascicles per brick: the brick's table and its offsets (gap-filled).
+__global__ void brick_fasc_kernel(const uint64_t* __restrict__ key2, int64_t m, int bf,
+                                  const int32_t* __restrict__ head, const int32_t* __restrict__ uidx, int32_t nb,
+                                  int32_t n_unique, int32_t* __restrict__ bptr, int32_t* __restrict__ bfasc) {
+    const uint64_t fmask = (1ull << bf) - 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key2[j];
+        const int32_t b = (int32_t)(k >> bf);
+        if (head[j]) bfasc[uidx[j]] = (int32_t)(k & fmask);
+        const int32_t bp = j == 0 ? -1 : (int32_t)(key2[j - 1] >> bf);
+        for (int32_t q = bp + 1; q <= b; ++q) bptr[q] = uidx[j];
+        if (j == m - 1)
+            for (int32_t q = b + 1; q <= nb; ++q) bptr[q] = n_unique;
+    }
+}
+
+// Brick-local fascicle number of each entry, scattered back to tile order.
+// uidx is the exclusive scan of the head flags, so an entry that repeats its
+// predecessor's (brick, fascicle) belongs to unique index uidx - 1.
+__global__ void local_fasc_kernel(const uint64_t* __restrict__ key2, const uint32_t* __restrict__ pay2, int64_t m,
+                                  int bf, const int32_t* __restrict__ head, const int32_t* __restrict__ uidx,
+                                  const int32_t* __restrict__ bptr, uint16_t* __restrict__ fl) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = (int32_t)(key2[j] >> bf);
+        const int32_t u = uidx[j] + head[j] - 1;
+        fl[pay2[j]] = (uint16_t)(u - bptr[b]);
+    }
+}
+
+// Entry streams in tile order, the continuation flag, and the sub-chunk offsets.
+__global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ spay, int64_t m,
+                                   int bf, const float* __restrict__ uval, int32_t n_sub, int64_t n_segs,
+                                   uint16_t* __restrict__ va, uint16_t* __restrict__ fl,
+                                   __nv_bfloat16* __restrict__ val, int32_t* __restrict__ sub_ptr) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = skey[j];
+        const uint64_t t = k >> (16 + bf);
+        const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
+        va[j] = (uint16_t)(row | (a << 7));
+        val[j] = __float2bfloat16_rn(uval[spay[j]]);
+        if (j > 0 && (skey[j - 1] >> bf) == (k >> bf)) fl[j] = (uint16_t)(fl[j] | CONT);
+        const int64_t seg = (int64_t)t * n_sub + (a >> 5);
+        int64_t segp = -1;
+        if (j > 0) {
+            const uint64_t kp = skey[j - 1];
+            segp = (int64_t)(kp >> (16 + bf)) * n_sub + (int64_t)(((kp >> (7 + bf)) & 511u) >> 5);
+        }
+        for (int64_t q = segp + 1; q <= seg; ++q) sub_ptr[q] = (int32_t)j;
+        if (j == m - 1)
+            for (int64_t q = seg + 1; q <= n_segs; ++q) sub_ptr[q] = (int32_t)m;
+    }
+}
+
+__global__ void fill_kernel(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+struct HostTiles {
+    std::vector<int32_t> tile_vox, vox_tile, vox_row, tile_brick, brick_tile_ptr;
+    int64_t n_tiles = 0, n_bricks = 0;
+};
+
+// Groups voxels into bricks (spatial B^3 cubes when coordinates are known,
+// else runs of B^3 consecutive voxel ids) and each brick into 128-voxel tiles.
+static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, int B, HostTiles& H) {
+    std::vector<int64_t> bkey(nv);
+    if (!ijk.empty()) {
+        int32_t mx[3] = {0, 0, 0};
+        for (int32_t v = 0; v < nv; ++v)
+            for (int d = 0; d < 3; ++d) mx[d] = std::max(mx[d], ijk[3 * v + d]);
+        const int64_t nbx = mx[0] / B + 1, nby = mx[1] / B + 1;
+        for (int32_t v = 0; v < nv; ++v)
+            bkey[v] = ((int64_t)(ijk[3 * v + 2] / B) * nby + ijk[3 * v + 1] / B) * nbx + ijk[3 * v] / B;
+    } else {
+        const int64_t bs = (int64_t)B * B * B;
+        for (int32_t v = 0; v < nv; ++v) bkey[v] = v / bs;
+    }
+    std::vector<int32_t> order(nv);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bkey[x] < bkey[y]; });
+    H.vox_tile.assign(nv, 0);
+    H.vox_row.assign(nv, 0);
+    H.tile_vox.clear();
+    H.tile_brick.clear();
+    H.brick_tile_ptr.assign(1, 0);
+    int64_t i = 0;
+    int32_t brick = 0;
+    while (i < nv) {
+        int64_t j = i;
+        while (j < nv && bkey[order[j]] == bkey[order[i]]) ++j;
+        for (int64_t s = i; s < j; s += TILE_V) {
+            const int32_t t = (int32_t)(H.tile_vox.size() / TILE_V);
+            for (int r = 0; r < TILE_V; ++r) {
+                const int64_t q = s + r;
+                if (q < j) {
+                    const int32_t v = order[q];
+                    H.tile_vox.push_back(v);
+                    H.vox_tile[v] = t;
+                    H.vox_row[v] = r;
+                } else {
+                    H.tile_vox.push_back(-1);
+                }
+            }
+            H.tile_brick.push_back(brick);
+        }
+        H.brick_tile_ptr.push_back((int32_t)(H.tile_vox.size() / TILE_V));
+        ++brick;
+        i = j;
+    }
+    H.n_tiles = (int64_t)H.tile_vox.size() / TILE_V;
+    H.n_bricks = brick;
+}
+
+template <class T>
+static life_status upload(DevBuf& dst, const std::vector<T>& src, cudaStream_t s) {
+    LIFE_TRY(dst.alloc(sizeof(T) * std::max<size_t>(src.size(), 1)));
+    if (!src.empty())
+        LIFE_CUDA_TRY(cudaMemcpyAsync(dst.p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return LIFE_OK;
+}
+
 life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
-    (void)ix; (void)s;
-    set_error("tensor-core layout not available in this build");
-    return LIFE_ENOTSUP;
+    TileLayout& L = ix->tile;
+    if (ix->na > 512 || ix->nt > 128) {
+        set_error("tensor-core path supports Na <= 512 and Ntheta <= 128 (got %d, %d)", ix->na, ix->nt);
+        return LIFE_ENOTSUP;
+    }
+    if (ix->key_bits_f > 32) {
+        set_error("tensor-core path: too many fascicles");
+        return LIFE_ENOTSUP;
+    }
+    const int64_t m = ix->nnz;
+    L.np = (ix->nt + 15) / 16 * 16;
+    L.kp = (ix->na + 127) / 128 * 128;   // whole 128-atom DSC chunks
+    L.n_sub = L.kp / SUB;
+    const int bf = ix->key_bits_f, ba = ix->key_bits_a, sa = bf, sv = bf + ba;
+    std::vector<int32_t> ijk;
+    if (ix->voxel_ijk.p) {
+        ijk.resize((size_t)ix->nv * 3);
+        LIFE_CUDA_TRY(cudaMemcpyAsync(ijk.data(), ix->voxel_ijk.p, sizeof(int32_t) * ijk.size(), cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    TmpBuf skey, spay;
+    LIFE_TRY(skey.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    LIFE_TRY(spay.alloc(sizeof(uint32_t) * std::max<int64_t>(m, 1), s));
+    HostTiles H;
+    std::vector<int32_t> hbptr;
+    DevBuf d_vox_tile, d_vox_row, d_tile_brick;
+    TmpBuf key2, pay2, head, uidx;
+    LIFE_TRY(key2.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    LIFE_TRY(pay2.alloc(sizeof(uint32_t) * std::max<int64_t>(m, 1), s));
+    LIFE_TRY(head.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    LIFE_TRY(uidx.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    int32_t n_unique = 0;
+    bool ok = false;
+    const int B0 = std::max(2, ix->brick_dim);
+    for (int B : {B0, B0 * 3 / 4, B0 / 2, B0 / 4}) {
+        if (B < 1) continue;
+        assign_tiles(ix->nv, ijk, B, H);
+        LIFE_TRY(upload(d_vox_tile, H.vox_tile, s));
+        LIFE_TRY(upload(d_vox_row, H.vox_row, s));
+        LIFE_TRY(upload(d_tile_brick, H.tile_brick, s));
+        const int bt = nbits64(H.n_tiles), bb = nbits64(H.n_bricks);
+        if (bt + 16 + bf > 64 || bb + bf > 64) {
+            set_error("tensor-core layout: sort key too wide");
+            return LIFE_ENOTSUP;
+        }
+        L.brick_fasc_ptr.release();
+        LIFE_TRY(L.brick_fasc_ptr.alloc(sizeof(int32_t) * (H.n_bricks + 1)));
+        if (m > 0) {
+            tile_key_kernel<<<grid1d(m), 256, 0, s>>>(ix->ukey.as<uint64_t>(), m, sa, sv, (1ull << ba) - 1,
+                                                      (1ull << bf) - 1, bf, d_vox_tile.as<int32_t>(),
+                                                      d_vox_row.as<int32_t>(), skey.as<uint64_t>(), spay.as<uint32_t>());
+            LIFE_CHECK_LAUNCH();
+            LIFE_TRY(radix_sort_pairs(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bt + 16 + bf, s));
+            brick_key_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), m, bf, d_tile_brick.as<int32_t>(),
+                                                       key2.as<uint64_t>(), pay2.as<uint32_t>());
+            LIFE_CHECK_LAUNCH();
+            LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bb + bf, s));
+            head_flag_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), m, head.as<int32_t>());
+            LIFE_CHECK_LAUNCH();
+            LIFE_TRY(exclusive_scan_i32(head.as<int32_t>(), uidx.as<int32_t>(), m, s));
+            int32_t last[2];
+            LIFE_CUDA_TRY(cudaMemcpyAsync(&last[0], uidx.as<int32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, s));
+            LIFE_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<int32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, s));
+            LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+            n_unique = last[0] + last[1];
+            L.brick_fasc.release();
+            LIFE_TRY(L.brick_fasc.alloc(sizeof(int32_t) * std::max(n_unique, 1)));
+            brick_fasc_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), m, bf, head.as<int32_t>(),
+                                                        uidx.as<int32_t>(), (int32_t)H.n_bricks, n_unique,
+                                                        L.brick_fasc_ptr.as<int32_t>(), L.brick_fasc.as<int32_t>());
+            LIFE_CHECK_LAUNCH();
+        } else {
+            fill_kernel<<<1, 256, 0, s>>>(L.brick_fasc_ptr.as<int32_t>(), H.n_bricks + 1, 0);
+            LIFE_CHECK_LAUNCH();
+            LIFE_TRY(L.brick_fasc.alloc(sizeof(int32_t)));
+        }
+        hbptr.resize(H.n_bricks + 1);
+        LIFE_CUDA_TRY(cudaMemcpyAsync(hbptr.data(), L.brick_fasc_ptr.p, sizeof(int32_t) * hbptr.size(),
+                                      cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+        int32_t mx = 0;
+        for (int64_t b = 0; b < H.n_bricks; ++b) mx = std::max(mx, hbptr[b + 1] - hbptr[b]);
+        L.max_fb = mx;
+        L.brick_edge = ijk.empty() ? 0 : B;
+        if (mx <= MAX_BRICK_FASC) {
+            ok = true;
+            break;
+        }
+    }
+    if (!ok) {
+        set_error("tensor-core layout: a brick touches %d fascicles (limit %d) even at the smallest brick",
+                  L.max_fb, MAX_BRICK_FASC);
+        return LIFE_ENOTSUP;
+    }
+    L.n_tiles = H.n_tiles;
+    L.n_bricks = H.n_bricks;
+    L.n_nnz = m;
+    const int64_t n_segs = H.n_tiles * L.n_sub;
+    // streams padded to whole 8-entry slots (the kernels load 16 bytes at a time)
+    const int64_t m_pad = (m + 7) / 8 * 8 + 8;
+    LIFE_TRY(L.va.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.fl.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.val.alloc(sizeof(__nv_bfloat16) * m_pad));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.va.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.fl.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+    LIFE_TRY(L.sub_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
+    if (m > 0) {
+        local_fasc_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
+                                                    head.as<int32_t>(), uidx.as<int32_t>(), L.brick_fasc_ptr.as<int32_t>(),
+                                                    L.fl.as<uint16_t>());
+        LIFE_CHECK_LAUNCH();
+        tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
+                                                     ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                     L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(),
+                                                     L.sub_ptr.as<int32_t>());
+        LIFE_CHECK_LAUNCH();
+    } else {
+        fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.sub_ptr.as<int32_t>(), n_segs + 1, 0);
+        LIFE_CHECK_LAUNCH();
+    }
+    LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
+    LIFE_TRY(upload(L.brick_tile_ptr, H.brick_tile_ptr, s));
+    // largest bricks first
+    std::vector<int32_t> tptr(H.n_tiles + 1);
+    {
+        std::vector<int32_t> sp(n_segs + 1);
+        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.sub_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int64_t t = 0; t <= H.n_tiles; ++t) tptr[t] = sp[t * L.n_sub];
+    }
+    std::vector<int64_t> bnnz(H.n_bricks);
+    for (int64_t b = 0; b < H.n_bricks; ++b)
+        bnnz[b] = (int64_t)tptr[H.brick_tile_ptr[b + 1]] - tptr[H.brick_tile_ptr[b]] +
+                  64 * (H.brick_tile_ptr[b + 1] - H.brick_tile_ptr[b]);
+    std::vector<int32_t> order(H.n_bricks);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bnnz[x] > bnnz[y]; });
+    LIFE_TRY(upload(L.brick_order, order, s));
+    LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    L.built = true;
+    return LIFE_OK;
 }
 
-life_status dsc_tc(life_index_s*, const float*, const float*, const float*, float*, double*, int*,
-                   const life_sbb_state*, int, cudaStream_t) {
-    set_error("tensor-core DSC not available in this build");
-    return LIFE_ENOTSUP;
+__global__ void widen_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t n, float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(in[i]);
 }
 
-life_status wc_tc(life_index_s*, const float*, const float*, float*, const life_sbb_state*, int, cudaStream_t) {
-    set_error("tensor-core WC not available in this build");
-    return LIFE_ENOTSUP;
+life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, int32_t* brick_tile_ptr,
+                         int32_t* brick_fasc_ptr, int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
+                         uint16_t* fl, float* val, cudaStream_t s) {
+    TileLayout& L = ix->tile;
+    auto cp = [&](void* dst, const DevBuf& src, size_t bytes) -> life_status {
+        if (dst && bytes) LIFE_CUDA_TRY(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToDevice, s));
+        return LIFE_OK;
+    };
+    LIFE_TRY(cp(tile_vox, L.tile_vox, sizeof(int32_t) * L.n_tiles * TILE_V));
+    LIFE_TRY(cp(sub_ptr, L.sub_ptr, sizeof(int32_t) * (L.n_tiles * L.n_sub + 1)));
+    LIFE_TRY(cp(brick_tile_ptr, L.brick_tile_ptr, sizeof(int32_t) * (L.n_bricks + 1)));
+    LIFE_TRY(cp(brick_fasc_ptr, L.brick_fasc_ptr, sizeof(int32_t) * (L.n_bricks + 1)));
+    LIFE_TRY(cp(brick_fasc, L.brick_fasc, L.brick_fasc.bytes));
+    LIFE_TRY(cp(brick_order, L.brick_order, sizeof(int32_t) * L.n_bricks));
+    LIFE_TRY(cp(va, L.va, sizeof(uint16_t) * L.n_nnz));
+    LIFE_TRY(cp(fl, L.fl, sizeof(uint16_t) * L.n_nnz));
+    if (val && L.n_nnz > 0) {
+        widen_bf16_kernel<<<grid1d(L.n_nnz), 256, 0, s>>>(L.val.as<__nv_bfloat16>(), L.n_nnz, val);
+        LIFE_CHECK_LAUNCH();
+    }
+    LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    return LIFE_OK;
+}
+
+// ================================================================ kernels
+
+struct TcArgs {
+    const int32_t* tile_vox;
+    const int32_t* sub_ptr;
+    const int32_t* brick_tile_ptr;
+    const int32_t* brick_fasc_ptr;
+    const int32_t* brick_fasc;
+    const int32_t* brick_order;
+    const uint16_t* va;
+    const uint16_t* fl;
+    const __nv_bfloat16* val;
+    const float* D;
+    const float* x;      // DSC: w [Nf];   WC: r [Nθ·Nv]
+    const float* b;      // DSC residual or NULL
+    float* out;          // DSC: y (or NULL);   WC: g (zeroed by the caller)
+    double* partial;     // DSC: per-CTA FP64 Σ out²
+    const life_sbb_state* gate;
+    int gate_mode;
+    uint32_t* status;
+    int nt, na, np, kp, n_sub, n_bricks, max_fb;
+    int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
+};
+
+// Brick processed by CTA c in round r (snake over the size-sorted list), or -1.
+__device__ __forceinline__ int brick_at(int r, int G, int c, int nb) {
+    const int k = r * G + ((r & 1) ? (G - 1 - c) : c);
+    return k < nb ? k : -1;
+}
+
+__device__ __forceinline__ uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Lane 0 waits (bounded) and the verdict is broadcast to the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, WAIT_LIMIT) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// ------------------------------------------------------------ entry slots
+// Producer and scatter threads read the entry streams 8 entries at a time with
+// 16-byte loads (the streams are padded to a multiple of 8 entries) and load
+// their next slot before working on the current one.
+
+constexpr int SLOT = 8;
+
+struct EntrySlot {
+    uint4 va, fl, val;
+};
+
+__device__ __forceinline__ void load_slot(const TcArgs& A, int base, EntrySlot& s) {
+    s.va = __ldg(reinterpret_cast<const uint4*>(A.va + base));
+    s.fl = __ldg(reinterpret_cast<const uint4*>(A.fl + base));
+    s.val = __ldg(reinterpret_cast<const uint4*>(A.val) + (base >> 3));
+}
+
+__device__ __forceinline__ uint32_t u16_at(const uint4& v, int e) {
+    const uint32_t w = e < 2 ? v.x : e < 4 ? v.y : e < 6 ? v.z : v.w;
+    return (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+__device__ __forceinline__ float bf16_at(const uint4& v, int e) { return __uint_as_float(u16_at(v, e) << 16); }
+
+__device__ __forceinline__ int chunk_beg(const TcArgs& A, int t, int c, int subs_per_chunk) {
+    return A.sub_ptr[(int64_t)t * A.n_sub + (int64_t)c * subs_per_chunk];
+}
+
+// Advances (r, brick, t, c) to the CTA's next chunk; false when none is left.
+__device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int n_c, int& r, int& brick, int& t,
+                                           int& c, bool& new_brick) {
+    new_brick = false;
+    if (++c < n_c) return true;
+    c = 0;
+    if (++t < A.brick_tile_ptr[brick + 1]) return true;
+    ++r;
+    const int k = brick_at(r, G, cta, A.n_bricks);
+    if (k < 0) return false;
+    brick = A.brick_order[k];
+    t = A.brick_tile_ptr[brick];
+    new_brick = true;
+    return true;
+}
+
+// ---------------------------------------------------------------------- DSC
+
+constexpr int DSC_PROD_WARPS = 15;   // 20 warps in all: 5 per SM sub-partition fit 96 registers
+constexpr int DSC_EPI_WARPS = 4;
+constexpr int DSC_MMA_WARP = DSC_PROD_WARPS + DSC_EPI_WARPS;
+constexpr int DSC_THREADS = (DSC_MMA_WARP + 1) * 32;
+constexpr int DSC_PROD_THREADS = DSC_PROD_WARPS * 32;
+constexpr int DKC = 128;                                  // atoms per DSC K chunk
+constexpr int DSTAGE = 2;                                 // S-chunk ring depth
+constexpr uint32_t DS_BYTES = TILE_V * DKC * 2;           // one S chunk: 128 rows x 128 atoms, bf16
+constexpr uint32_t DS_SBO = (DKC / 8) * 128;              // 8-row group stride of an S chunk
+
+__host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb) {
+    uint32_t d = (uint32_t)np * kp * 2;
+    d = (d + 1023) / 1024 * 1024;
+    return d + DSTAGE * DS_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+}
+
+__device__ __forceinline__ void store_s(unsigned char* S, uint32_t va, float s, int c) {
+    const uint32_t row = va & 127u, al = (va >> 7) - (uint32_t)(c * DKC);
+    *reinterpret_cast<__nv_bfloat16*>(S + kmajor_off(row, al, DS_SBO)) = __float2bfloat16_rn(s);
+}
+
+// S[a, row] for the runs that start inside this slot (a run = entries with the
+// same (atom, row)); a run that goes on past the slot is finished from memory.
+__device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, int base, int beg, int end,
+                                         const float* wl, unsigned char* S, int c) {
+    bool have = false;
+    uint32_t cva = 0;
+    float cs = 0.0f;
+#pragma unroll
+    for (int e = 0; e < SLOT; ++e) {
+        const int idx = base + e;
+        if (idx < beg || idx >= end) continue;
+        const uint32_t f = u16_at(s.fl, e);
+        const float x = bf16_at(s.val, e);
+        if (f & CONT) {
+            if (have) cs = fmaf(x, wl[f & 0x7FFFu], cs);
+        } else {
+            if (have) store_s(S, cva, cs, c);
+            have = true;
+            cva = u16_at(s.va, e);
+            cs = x * wl[f];
+        }
+    }
+    if (have) {
+        for (int j = base + SLOT; j < end; ++j) {
+            const uint32_t f = A.fl[j];
+            if (!(f & CONT)) break;
+            cs = fmaf(__bfloat162float(A.val[j]), wl[f & 0x7FFFu], cs);
+        }
+        store_s(S, cva, cs, c);
+    }
+}
+
+__global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, never;
+    __shared__ double red[DSC_EPI_WARPS];
+    if (gate_skip(A.gate, A.gate_mode)) return;
+    const bool write_y = A.out != nullptr && !(A.gate && A.gate_mode == 3 && A.gate->eq != 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t d_bytes = align_up((uint32_t)A.np * A.kp * 2, 1024);
+    unsigned char* Ds = smem;
+    unsigned char* Ss = smem + d_bytes;
+    float* wl = reinterpret_cast<float*>(Ss + DSTAGE * DS_BYTES);
+    const uint32_t SBO_D = (uint32_t)(A.kp / 8) * 128u;
+
+    // D as the B operand: rows θ (N), K = atoms; bf16, zero-padded.
+    for (int i = tid; i < A.np * A.kp; i += blockDim.x) {
+        const int t = i % A.np, a = i / A.np;
+        const float d = (t < A.nt && a < A.na) ? A.D[t + (int64_t)A.nt * a] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(Ds + kmajor_off(t, a, SBO_D)) = __float2bfloat16_rn(d);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < DSTAGE; ++s) {
+            mbar_init(&full_bar[s], DSC_PROD_WARPS);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], DSC_EPI_WARPS);
+        }
+        mbar_init(&fin_bar, 1);
+        abort_flag = 0;
+        never = 0;
+        fence_barrier_init();
+    }
+    if (warp == DSC_MMA_WARP) {
+        tmem_alloc(&tmem_base, 256);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = tmem_base;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int n_c = A.kp / DKC;
+    const int spc = DKC / SUB;  // sub-chunks per chunk
+    double sq = 0.0;
+
+    if (warp < DSC_PROD_WARPS) {
+        // ---------------- producers: S[a, row] = Σ val·w for one 128-atom chunk
+        int r = 0;
+        const int k0 = brick_at(0, G, cta, A.n_bricks);
+        if (k0 >= 0) {
+            int brick = A.brick_order[k0], t = A.brick_tile_ptr[brick], c = 0;
+            int beg = chunk_beg(A, t, 0, spc), end = chunk_beg(A, t, 1, spc);
+            int base = (beg & ~7) + tid * SLOT;
+            bool have = base < end;
+            EntrySlot cur;
+            if (have) load_slot(A, base, cur);
+            bool new_brick = true;
+            uint32_t cc = 0;
+            for (;;) {
+                if (new_brick) {
+                    const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
+                    named_bar_sync(1, DSC_PROD_THREADS);
+                    for (int i = tid; i < nfb; i += DSC_PROD_THREADS) wl[i] = __ldg(A.x + A.brick_fasc[fb0 + i]);
+                    named_bar_sync(1, DSC_PROD_THREADS);
+                }
+                const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
+                unsigned char* S = Ss + st * DS_BYTES;
+                const bool fail = !warp_wait(&empty_bar[st], ph ^ 1u, &abort_flag);
+                if (!fail) {
+                    uint4* z = reinterpret_cast<uint4*>(S);
+                    for (int q = tid; q < (int)(DS_BYTES / 16); q += DSC_PROD_THREADS) z[q] = make_uint4(0, 0, 0, 0);
+                }
+                if (named_bar_or(1, DSC_PROD_THREADS, fail || abort_flag != 0)) {
+                    abort_flag = 1;
+                    break;
+                }
+                int nr = r, nbrick = brick, nt = t, nc = c;
+                bool nnew = false;
+                const bool nvalid = next_chunk(A, G, cta, n_c, nr, nbrick, nt, nc, nnew);
+                int nbeg = 0, nend = 0;
+                if (nvalid) {
+                    nbeg = chunk_beg(A, nt, nc, spc);
+                    nend = chunk_beg(A, nt, nc + 1, spc);
+                }
+                const int nbase = (nbeg & ~7) + tid * SLOT;
+                const bool nhave = nvalid && nbase < nend;
+                EntrySlot nxt;
+                bool pf = false;
+                while (have) {
+                    const int b2 = base + DSC_PROD_THREADS * SLOT;
+                    const bool more = b2 < end;
+                    if (more) load_slot(A, b2, nxt);
+                    else if (nhave) {
+                        load_slot(A, nbase, nxt);
+                        pf = true;
+                    }
+                    dsc_slot(A, cur, base, beg, end, wl, S, c);
+                    if (!more) break;
+                    cur = nxt;
+                    base = b2;
+                }
+                if (!pf && nhave) load_slot(A, nbase, nxt);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[st]);
+                ++cc;
+                if (!nvalid) break;
+                r = nr;
+                brick = nbrick;
+                t = nt;
+                c = nc;
+                beg = nbeg;
+                end = nend;
+                new_brick = nnew;
+                base = nbase;
+                have = nhave;
+                if (have) cur = nxt;
+            }
+        }
+    } else if (warp < DSC_MMA_WARP) {
+        // ---------------- epilogue: TMEM -> y (− b), Σ y² (FP32 per row and tile, FP64 across)
+        const int q = warp & 3;  // TMEM lanes 32q .. 32q+31
+        const int row = 32 * q + lane;
+        const bool vec = A.vec4 != 0;
+        uint32_t tcount = 0;
+        bool stop = false;
+        for (int r = 0; !stop; ++r) {
+            const int k = brick_at(r, G, cta, A.n_bricks);
+            if (k < 0) break;
+            const int brick = A.brick_order[k];
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
+                const uint32_t ab = tcount & 1u, aph = (tcount >> 1) & 1u;
+                if (!warp_wait(&acc_full[ab], aph, &abort_flag)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const int v = A.tile_vox[(int64_t)t * TILE_V + row];
+                const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + ab * 128u;
+                float sqf = 0.0f;
+                for (int j = 0; j < A.np; j += 32) {
+                    uint32_t rr[32];
+                    int cnt = 32;
+                    if (A.np - j >= 32) {
+                        tmem_ld32(taddr + j, rr);
+                    } else {
+                        uint32_t r16[16];
+                        tmem_ld16(taddr + j, r16);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) rr[e] = r16[e];
+                        cnt = 16;
+                    }
+                    tmem_ld_wait();
+                    if (v < 0) continue;
+                    const int64_t o = (int64_t)A.nt * v + j;
+                    if (vec && j + cnt <= A.nt) {
+                        for (int e = 0; e < cnt; e += 4) {
+                            float4 yv = make_float4(__uint_as_float(rr[e]), __uint_as_float(rr[e + 1]),
+                                                    __uint_as_float(rr[e + 2]), __uint_as_float(rr[e + 3]));
+                            if (A.b) {
+                                const float4 bv = __ldg(reinterpret_cast<const float4*>(A.b + o + e));
+                                yv.x -= bv.x;
+                                yv.y -= bv.y;
+                                yv.z -= bv.z;
+                                yv.w -= bv.w;
+                            }
+                            if (write_y) *reinterpret_cast<float4*>(A.out + o + e) = yv;
+                            sqf += yv.x * yv.x + yv.y * yv.y + yv.z * yv.z + yv.w * yv.w;
+                        }
+                    } else {
+                        for (int e = 0; e < cnt; ++e) {
+                            if (j + e < A.nt) {
+                                float y = __uint_as_float(rr[e]);
+                                if (A.b) y -= A.b[o + e];
+                                if (write_y) A.out[o + e] = y;
+                                sqf += y * y;
+                            }
+                        }
+                    }
+                }
+                sq += (double)sqf;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[ab]);
+                ++tcount;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[q] = sq;
+    } else if (lane == 0) {
+        // ---------------- MMA issuer: Yᵀ[128 x np] = S[128 x kp] · Dᵀ
+        const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)A.np);
+        const uint32_t sS = smem_u32(Ss), sD = smem_u32(Ds);
+        uint32_t cc = 0, tcount = 0;
+        bool stop = false;
+        for (int r = 0; !stop; ++r) {
+            const int k = brick_at(r, G, cta, A.n_bricks);
+            if (k < 0) break;
+            const int brick = A.brick_order[k];
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1] && !stop; ++t) {
+                const uint32_t ab = tcount & 1u, aph = (tcount >> 1) & 1u;
+                if (!mbar_wait(&acc_empty[ab], aph ^ 1u, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
+                tc_fence_after();
+                const uint32_t d = tb + ab * 128u;
+                for (int c = 0; c < n_c; ++c) {
+                    const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
+                    if (!mbar_wait(&full_bar[st], ph, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
+                    tc_fence_after();
+#pragma unroll
+                    for (int kk = 0; kk < DKC / 16; ++kk) {
+                        const uint64_t ad = smem_desc(sS + st * DS_BYTES + kk * 256u, 128u, DS_SBO);
+                        const uint64_t bd = smem_desc(sD + (uint32_t)c * (DKC / 8) * 128u + kk * 256u, 128u, SBO_D);
+                        mma_bf16(d, ad, bd, idesc, (c | kk) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(&empty_bar[st]);
+                    ++cc;
+                }
+                if (stop) break;
+                mma_commit(&acc_full[ab]);
+                ++tcount;
+            }
+        }
+        mma_commit(&fin_bar);
+        mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT);
+    }
+    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == DSC_MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tb, 256);
+    }
+    if (tid == 0 && A.partial) {
+        double tot = 0.0;
+        for (int e = 0; e < DSC_EPI_WARPS; ++e) tot += red[e];
+        A.partial[blockIdx.x] = tot;
+    }
+}
+
+// ----------------------------------------------------------------------- WC
+
+constexpr int WC_SCAT_WARPS = 16;
+constexpr int WC_LOAD_WARPS = 3;     // 20 warps in all (see DSC_PROD_WARPS)
+constexpr int WC_MMA_WARP = WC_SCAT_WARPS + WC_LOAD_WARPS;
+constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
+constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
+constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
+constexpr uint32_t ZC_BYTES = TILE_V * ZSTRIDE * 4;
+
+__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb) {
+    uint32_t d = (uint32_t)kp * np * 2;
+    d = (d + 1023) / 1024 * 1024;
+    uint32_t r = (uint32_t)TILE_V * np * 2;
+    r = (r + 1023) / 1024 * 1024;
+    return d + r + 2 * ZC_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
+                                        int sub) {
+#pragma unroll
+    for (int e = 0; e < SLOT; ++e) {
+        const int idx = base + e;
+        if (idx < beg || idx >= end) continue;
+        const uint32_t v16 = u16_at(s.va, e);
+        const uint32_t row = v16 & 127u, al = (v16 >> 7) - (uint32_t)(SUB * sub);
+        const float p = bf16_at(s.val, e) * Z[row * ZSTRIDE + al];
+        atomicAdd(&gl[u16_at(s.fl, e) & 0x7FFFu], p);
+    }
+}
+
+__global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t r_full, r_empty, z_full, z_empty, fin_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, never;
+    if (gate_skip(A.gate, A.gate_mode)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t d_bytes = align_up((uint32_t)A.kp * A.np * 2, 1024);
+    const uint32_t r_bytes = align_up((uint32_t)TILE_V * A.np * 2, 1024);
+    unsigned char* Dw = smem;
+    unsigned char* Rs = smem + d_bytes;
+    float* Zc = reinterpret_cast<float*>(Rs + r_bytes);
+    float* gl = Zc + 2 * TILE_V * ZSTRIDE;
+    const uint32_t SBO_K = (uint32_t)(A.np / 8) * 128u;  // 8-row groups of both operands (K = θ)
+
+    // D as the B operand: rows = atoms (N), K = θ; bf16, zero-padded.
+    for (int i = tid; i < A.kp * A.np; i += blockDim.x) {
+        const int t = i % A.np, a = i / A.np;
+        const float d = (t < A.nt && a < A.na) ? A.D[t + (int64_t)A.nt * a] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(Dw + kmajor_off(a, t, SBO_K)) = __float2bfloat16_rn(d);
+    }
+    if (tid == 0) {
+        mbar_init(&r_full, WC_LOAD_WARPS);
+        mbar_init(&r_empty, 1);
+        mbar_init(&z_full, 1);
+        mbar_init(&z_empty, 1);
+        mbar_init(&fin_bar, 1);
+        abort_flag = 0;
+        never = 0;
+        fence_barrier_init();
+    }
+    if (warp == WC_MMA_WARP) {
+        tmem_alloc(&tmem_base, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = tmem_base;
+    const int G = gridDim.x, cta = blockIdx.x;
+
+    if (warp < WC_SCAT_WARPS) {
+        // ---------------- Z chunks out of TMEM, then g_local[f] += val·Z[a, row]
+        const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q..; columns 8h .. 8h+7 of each sub-chunk
+        int r = 0;
+        const int k0 = brick_at(0, G, cta, A.n_bricks);
+        if (k0 >= 0) {
+            int brick = A.brick_order[k0], t = A.brick_tile_ptr[brick], sub = 0;
+            int beg = chunk_beg(A, t, 0, 1), end = chunk_beg(A, t, 1, 1);
+            int base = (beg & ~7) + tid * SLOT;
+            bool have = base < end;
+            EntrySlot cur;
+            if (have) load_slot(A, base, cur);
+            bool new_brick = true, stop = false;
+            uint32_t tcount = 0, zc = 0;
+            int fb0 = 0, nfb = 0;
+            for (;;) {
+                if (new_brick) {
+                    fb0 = A.brick_fasc_ptr[brick];
+                    nfb = A.brick_fasc_ptr[brick + 1] - fb0;
+                    named_bar_sync(2, WC_SCAT_THREADS);
+                    for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
+                    named_bar_sync(2, WC_SCAT_THREADS);
+                }
+                if (sub == 0) {
+                    const bool fail = !warp_wait(&z_full, tcount & 1u, &abort_flag);
+                    if (named_bar_or(2, WC_SCAT_THREADS, fail || abort_flag != 0)) {
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                float* Z = Zc + (zc & 1u) * (TILE_V * ZSTRIDE);
+                {
+                    uint32_t r8[8];
+                    tmem_ld8(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(SUB * sub + 8 * h), r8);
+                    tmem_ld_wait();
+                    float* zrow = Z + (32 * q + lane) * ZSTRIDE + 8 * h;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) zrow[e] = __uint_as_float(r8[e]);
+                }
+                const bool last_sub = sub == A.n_sub - 1;
+                if (last_sub) tc_fence_before();
+                named_bar_sync(2, WC_SCAT_THREADS);
+                if (last_sub && tid == 0) mbar_arrive(&z_empty);  // TMEM free for the next tile
+                int nr = r, nbrick = brick, nt = t, nsub = sub;
+                bool nnew = false;
+                const bool nvalid = next_chunk(A, G, cta, A.n_sub, nr, nbrick, nt, nsub, nnew);
+                int nbeg = 0, nend = 0;
+                if (nvalid) {
+                    nbeg = chunk_beg(A, nt, nsub, 1);
+                    nend = chunk_beg(A, nt, nsub + 1, 1);
+                }
+                const int nbase = (nbeg & ~7) + tid * SLOT;
+                const bool nhave = nvalid && nbase < nend;
+                EntrySlot nxt;
+                bool pf = false;
+                while (have) {
+                    const int b2 = base + WC_SCAT_THREADS * SLOT;
+                    const bool more = b2 < end;
+                    if (more) load_slot(A, b2, nxt);
+                    else if (nhave) {
+                        load_slot(A, nbase, nxt);
+                        pf = true;
+                    }
+                    wc_slot(cur, base, beg, end, Z, gl, sub);
+                    if (!more) break;
+                    cur = nxt;
+                    base = b2;
+                }
+                if (!pf && nhave) load_slot(A, nbase, nxt);
+                ++zc;
+                if (last_sub) ++tcount;
+                if (!nvalid || nnew) {
+                    // brick done: flush its fascicle sums to g with one atomic each
+                    if (named_bar_or(2, WC_SCAT_THREADS, abort_flag != 0)) {
+                        stop = true;
+                        break;
+                    }
+                    for (int i = tid; i < nfb; i += WC_SCAT_THREADS) {
+                        const float gv = gl[i];
+                        if (gv != 0.0f) atomicAdd(A.out + A.brick_fasc[fb0 + i], gv);
+                    }
+                }
+                if (!nvalid) break;
+                r = nr;
+                brick = nbrick;
+                t = nt;
+                sub = nsub;
+                beg = nbeg;
+                end = nend;
+                new_brick = nnew;
+                base = nbase;
+                have = nhave;
+                if (have) cur = nxt;
+            }
+            (void)stop;
+        }
+    } else if (warp < WC_MMA_WARP) {
+        // ---------------- R tile loader: r[:, v] -> bf16 A operand (rows = voxels, K = θ)
+        const int lt = tid - WC_SCAT_THREADS;
+        const int ngrp = A.np / 8;
+        const bool vec = A.vec4 != 0 && (A.nt % 8) == 0;
+        uint32_t tcount = 0;
+        bool stop = false;
+        for (int r = 0; !stop; ++r) {
+            const int k = brick_at(r, G, cta, A.n_bricks);
+            if (k < 0) break;
+            const int brick = A.brick_order[k];
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
+                if (!warp_wait(&r_empty, (tcount & 1u) ^ 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                const int total = TILE_V * ngrp;
+                for (int u0 = lt; u0 < total; u0 += 4 * WC_LOAD_THREADS) {
+                    float4 lo[4], hi[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const int u = u0 + s * WC_LOAD_THREADS;
+                        lo[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        hi[s] = lo[s];
+                        if (u < total) {
+                            const int row = u / ngrp, g8 = u % ngrp;
+                            const int v = A.tile_vox[(int64_t)t * TILE_V + row];
+                            if (v >= 0) {
+                                const float* src = A.x + (int64_t)A.nt * v + 8 * g8;
+                                if (vec && 8 * g8 + 8 <= A.nt) {
+                                    lo[s] = __ldg(reinterpret_cast<const float4*>(src));
+                                    hi[s] = __ldg(reinterpret_cast<const float4*>(src) + 1);
+                                } else {
+                                    float e[8];
+#pragma unroll
+                                    for (int z = 0; z < 8; ++z) e[z] = (8 * g8 + z < A.nt) ? src[z] : 0.0f;
+                                    lo[s] = make_float4(e[0], e[1], e[2], e[3]);
+                                    hi[s] = make_float4(e[4], e[5], e[6], e[7]);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const int u = u0 + s * WC_LOAD_THREADS;
+                        if (u >= total) continue;
+                        const int row = u / ngrp, g8 = u % ngrp;
+                        __nv_bfloat162 p0 = __floats2bfloat162_rn(lo[s].x, lo[s].y);
+                        __nv_bfloat162 p1 = __floats2bfloat162_rn(lo[s].z, lo[s].w);
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(hi[s].x, hi[s].y);
+                        __nv_bfloat162 p3 = __floats2bfloat162_rn(hi[s].z, hi[s].w);
+                        uint4 pk;
+                        pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                        pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                        pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                        pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                        *reinterpret_cast<uint4*>(Rs + kmajor_off(row, 8 * g8, SBO_K)) = pk;
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&r_full);
+                ++tcount;
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer: Zᵀ[128 x kp] = R[128 x np] · Dᵀ (kp split in N <= 256 pieces)
+        const int nh = A.kp <= 256 ? A.kp : A.kp / 2;
+        const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)nh);
+        const uint32_t sR = smem_u32(Rs), sD = smem_u32(Dw);
+        uint32_t tcount = 0;
+        bool stop = false;
+        for (int r = 0; !stop; ++r) {
+            const int k = brick_at(r, G, cta, A.n_bricks);
+            if (k < 0) break;
+            const int brick = A.brick_order[k];
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
+                const uint32_t ph = tcount & 1u;
+                if (!mbar_wait(&r_full, ph, &abort_flag, WAIT_LIMIT) ||
+                    !mbar_wait(&z_empty, ph ^ 1u, &abort_flag, WAIT_LIMIT)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                for (int n0 = 0; n0 < A.kp; n0 += nh) {
+                    for (int kk = 0; kk < A.np / 16; ++kk) {
+                        const uint64_t ad = smem_desc(sR + kk * 256u, 128u, SBO_K);
+                        const uint64_t bd = smem_desc(sD + (uint32_t)(n0 / 8) * SBO_K + kk * 256u, 128u, SBO_K);
+                        mma_bf16(tb + (uint32_t)n0, ad, bd, idesc, kk != 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(&r_empty);
+                mma_commit(&z_full);
+                ++tcount;
+            }
+        }
+        mma_commit(&fin_bar);
+        mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT);
+    }
+    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == WC_MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tb, 512);
+    }
+}
+
+// ============================================================== launchers
+
+static TcArgs make_args(life_index_s* ix) {
+    TileLayout& L = ix->tile;
+    TcArgs A{};
+    A.tile_vox = L.tile_vox.as<int32_t>();
+    A.sub_ptr = L.sub_ptr.as<int32_t>();
+    A.brick_tile_ptr = L.brick_tile_ptr.as<int32_t>();
+    A.brick_fasc_ptr = L.brick_fasc_ptr.as<int32_t>();
+    A.brick_fasc = L.brick_fasc.as<int32_t>();
+    A.brick_order = L.brick_order.as<int32_t>();
+    A.va = L.va.as<uint16_t>();
+    A.fl = L.fl.as<uint16_t>();
+    A.val = L.val.as<__nv_bfloat16>();
+    A.nt = ix->nt;
+    A.na = ix->na;
+    A.np = L.np;
+    A.kp = L.kp;
+    A.n_sub = L.n_sub;
+    A.n_bricks = (int)L.n_bricks;
+    A.max_fb = L.max_fb;
+    A.status = dev_status_word();
+    return A;
+}
+
+life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
+                   int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
+    TcArgs A = make_args(ix);
+    if (!A.status) {
+        set_error("dsc_tc: no device status word");
+        return LIFE_ENOMEM;
+    }
+    A.D = D;
+    A.x = w;
+    A.b = b;
+    A.out = y;
+    A.partial = partial;
+    A.gate = gate;
+    A.gate_mode = gate_mode;
+    A.vec4 = (ix->nt % 4 == 0 && ((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) ? 1 : 0;
+    const uint32_t smem = dsc_smem_bytes(A.np, A.kp, A.max_fb);
+    LIFE_CUDA_TRY(cudaFuncSetAttribute(dsc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
+    dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+    LIFE_CHECK_LAUNCH();
+    if (n_partial) *n_partial = grid;
+    return LIFE_OK;
+}
+
+life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate, int gate_mode,
+                  cudaStream_t s) {
+    TcArgs A = make_args(ix);
+    if (!A.status) {
+        set_error("wc_tc: no device status word");
+        return LIFE_ENOMEM;
+    }
+    A.D = D;
+    A.x = r;
+    A.out = g;
+    A.gate = gate;
+    A.gate_mode = gate_mode;
+    A.vec4 = (ix->nt % 4 == 0 && (reinterpret_cast<uintptr_t>(r) & 15) == 0) ? 1 : 0;
+    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb);
+    LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
+    wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
 }
 
 }  // namespace life

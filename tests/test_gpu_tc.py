@@ -1,0 +1,238 @@
+"""GPU parity of the tensor-core (BF16-storage) path against the FP64 oracle.
+
+Tolerance: relative L2 error <= 3e-3 for the reduced-precision path (Φ values, D,
+and the on-chip S / r tiles are BF16; accumulation is FP32; reductions FP64).
+Every call is followed by a device-status check, so a bounded wait that gave up
+inside a kernel fails the test instead of passing silently.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16 = 3e-3
+U_BF16 = 2.0 ** -8   # unit roundoff of BF16 (8 significand bits, round to nearest)
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def life():
+    import paper_1905_06234_gb300 as L
+    L.load(build_if_missing=True)
+    return L
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def tc_index(life, a, v, f, x, nt, na, nv, nf, ijk=None):
+    idx = life.index_from_arrays(a, v, f, x, nt, na, nv, nf, voxel_ijk=ijk, precision=life.LIFE_BF16,
+                                 algo=life.LIFE_ALGO_TC)
+    assert idx.info()["algo"] == life.LIFE_ALGO_TC
+    return idx
+
+
+def rounding_bounds(phi, D32, w, r, nt, nv, nf):
+    """First-order bounds on |GPU - exact| per output element.  DSC rounds three
+    quantities to BF16 (the Phi value, S = sum val*w, and D): |err| <= 3u sum|D||val w|.
+    WC rounds the value, D and r: |err| <= 3u sum_k |val| sum_t |D||r|.  FP32
+    accumulation adds far less and is covered by the factor 1.25."""
+    a = np.abs
+    yb = oracle.dsc(oracle.Phi(phi.atom, phi.voxel, phi.fasc, a(phi.val)), a(D32), a(w), nt, nv)
+    gb = oracle.wc(oracle.Phi(phi.atom, phi.voxel, phi.fasc, a(phi.val)), a(D32), a(r), nt, nf)
+    return 1.25 * 3 * U_BF16 * yb, 1.25 * 3 * U_BF16 * gb
+
+
+def run_check(life, idx, phi, D32, nt, nv, nf, seed=0, tol=TOL_BF16, elementwise=False):
+    rng = np.random.default_rng(seed)
+    w = rng.random(nf).astype(np.float32)
+    w[rng.random(nf) < 0.3] = 0.0
+    r = rng.standard_normal(nt * nv).astype(np.float32)
+    b = rng.standard_normal(nt * nv).astype(np.float32)
+    D = dev(D32)
+    y, ss = life.life_dsc(idx, D, dev(w), sumsq=True)
+    e, _ = life.life_dsc(idx, D, dev(w), b=dev(b))
+    g, ssg = life.life_wc(idx, D, dev(r), sumsq=True)
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    y_ref = oracle.dsc(phi, D32, w, nt, nv)
+    g_ref = oracle.wc(phi, D32, r, nt, nf)
+    errs = dict(y=rel(y.cpu().numpy(), y_ref), e=rel(e.cpu().numpy(), y_ref - b), g=rel(g.cpu().numpy(), g_ref),
+                ss=abs(float(ss) - y_ref @ y_ref) / max(y_ref @ y_ref, 1e-30),
+                ssg=abs(float(ssg) - g_ref @ g_ref) / max(g_ref @ g_ref, 1e-30))
+    yb, gb = rounding_bounds(phi, D32, w, r, nt, nv, nf)
+    assert (np.abs(y.cpu().numpy() - y_ref) <= yb + 1e-30).all()
+    assert (np.abs(g.cpu().numpy() - g_ref) <= gb + 1e-30).all()
+    if elementwise:   # degenerate shapes: too few terms for the statistical L2 bound
+        return errs
+    assert errs["y"] <= tol and errs["e"] <= tol and errs["g"] <= tol, errs
+    assert errs["ss"] <= 2 * tol and errs["ssg"] <= 2 * tol, errs
+    return errs
+
+
+def test_tc_tiny_workload(life):
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    idx = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                   p.n_fasc, ijk=p.voxel_ijk)
+    info = idx.info()
+    assert info["n_bricks"] == 8 and info["n_tiles"] == 32   # 16^3 grid in 8^3 bricks of 4 tiles
+    print(run_check(life, idx, phi, D32, p.n_theta, p.n_voxels, p.n_fasc))
+
+
+def raw_problem(nt, na, nv, nf, nnz, seed):
+    rng = np.random.default_rng(seed)
+    live_v = rng.permutation(nv)[: max(1, int(nv * 0.9))]
+    a = rng.integers(0, na, nnz).astype(np.int32)
+    v = live_v[rng.integers(0, len(live_v), nnz)].astype(np.int32)
+    f = rng.integers(0, nf, nnz).astype(np.int32)
+    x = rng.uniform(0.5, 1.0, nnz).astype(np.float32)
+    return a, v, f, x
+
+
+@pytest.mark.parametrize("shape", [(96, 360, 1000, 300, 30000), (16, 7, 130, 50, 2000), (33, 64, 257, 1031, 20011),
+                                   (128, 512, 300, 400, 60000), (1, 1, 5, 3, 40), (64, 100, 3000, 20000, 150000)])
+def test_tc_shapes(life, shape):
+    nt, na, nv, nf, nnz = shape
+    a, v, f, x = raw_problem(nt, na, nv, nf, nnz, seed=nnz)
+    phi = oracle.canon(a, v, f, x, na, nv, nf)
+    D32 = np.random.default_rng(1).standard_normal(nt * na).astype(np.float32)
+    idx = tc_index(life, a, v, f, x, nt, na, nv, nf)
+    run_check(life, idx, phi, D32, nt, nv, nf, elementwise=nt < 8)
+
+
+def test_tc_giant_voxel_and_empty(life):
+    nt, na, nv, nf = 96, 360, 700, 3000
+    rng = np.random.default_rng(5)
+    n = 80000
+    v = np.where(rng.random(n) < 0.7, 333, rng.integers(0, 600, n)).astype(np.int32)   # voxels 600.. empty
+    a = rng.integers(0, na, n).astype(np.int32)
+    f = rng.integers(0, nf, n).astype(np.int32)
+    x = rng.uniform(0.5, 1, n).astype(np.float32)
+    phi = oracle.canon(a, v, f, x, na, nv, nf)
+    D32 = rng.standard_normal(nt * na).astype(np.float32)
+    idx = tc_index(life, a, v, f, x, nt, na, nv, nf)
+    run_check(life, idx, phi, D32, nt, nv, nf)
+    # an index with no entries at all
+    idx0 = tc_index(life, a[:0], v[:0], f[:0], x[:0], nt, na, nv, nf)
+    y, _ = life.life_dsc(idx0, dev(D32), torch.ones(nf, device="cuda"))
+    g, _ = life.life_wc(idx0, dev(D32), torch.ones(nt * nv, device="cuda"))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    assert float(y.abs().max()) == 0.0 and float(g.abs().max()) == 0.0
+
+
+def test_tc_matches_simt_bf16_values(life):
+    """Same BF16-rounded Φ values on both paths: the remaining difference is the
+    BF16 rounding of D and of the on-chip S / r tiles."""
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    i_tc = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                    p.n_fasc, ijk=p.voxel_ijk)
+    i_st = life.upload_problem(p, precision=life.LIFE_BF16, algo=life.LIFE_ALGO_SIMT)
+    w = dev(p.w_true)
+    y1, _ = life.life_dsc(i_tc, dev(D32), w)
+    y2, _ = life.life_dsc(i_st, dev(D32), w)
+    torch.cuda.synchronize()
+    assert rel(y1.cpu().numpy(), y2.cpu().numpy()) <= TOL_BF16
+
+
+def test_tc_sbb_teacher_forced(life):
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    b = oracle.problem_signal(phi, D32, p.w_true, p.noise, p.n_theta, p.n_voxels)
+    idx = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                   p.n_fasc, ijk=p.voxel_ijk)
+    w = torch.ones(p.n_fasc, device="cuda")
+    st, ws = life.new_sbb_state(), life.new_sbb_workspace(idx)
+    ost = oracle.SbbState()
+    worst = 0.0
+    for it in range(6):
+        w_in = w.double().cpu().numpy().copy()
+        prev = life.read_sbb_state(st)
+        ost.s.it, ost.s.alpha, ost.s.gg0 = prev["it"], prev["alpha"], prev["gg0"]
+        life.life_sbbnnls_step(idx, dev(D32), dev(b), w, st, ws)
+        torch.cuda.synchronize()
+        oracle.sbb_step(phi, D32, b, w_in, p.n_theta, p.n_voxels, p.n_fasc, ost)
+        gst = life.read_sbb_state(st)
+        assert gst["eq"] == ost.eq
+        for k in ("obj", "gg", "vv", "alpha"):
+            worst = max(worst, abs(gst[k] - getattr(ost, k)) / abs(getattr(ost, k)))
+    life.life_check_device_status()
+    # g carries the BF16 error of WC plus the DSC error of e = Mw - b amplified by
+    # |Mw| / |e|; <g~,g~> doubles the relative error: a few times 3e-3
+    assert worst <= 3e-2, worst
+
+
+def expected_tiles(phi, tile_vox, brick_tile_ptr, nv, n_sub):
+    """The tile layout the restructuring must produce, rebuilt on the host from the
+    oracle's merged Phi and the library's voxel -> (tile, row) assignment."""
+    n_tiles = len(tile_vox) // 128
+    vox_tile = np.full(nv, -1, np.int64)
+    vox_row = np.full(nv, -1, np.int64)
+    for t in range(n_tiles):
+        for r in range(128):
+            v = tile_vox[128 * t + r]
+            if v >= 0:
+                assert vox_tile[v] == -1, "voxel placed twice"
+                vox_tile[v], vox_row[v] = t, r
+    assert (vox_tile >= 0).all(), "voxel missing from the tiles"
+    tile_brick = np.repeat(np.arange(len(brick_tile_ptr) - 1), np.diff(brick_tile_ptr))
+    t = vox_tile[phi.voxel]
+    row = vox_row[phi.voxel]
+    a = phi.atom.astype(np.int64)
+    f = phi.fasc.astype(np.int64)
+    order = np.lexsort((f, row, a, t))
+    t, row, a, f, val = t[order], row[order], a[order], f[order], phi.val[order]
+    va = (row | (a << 7)).astype(np.uint16)
+    b = tile_brick[t]
+    bfk = np.unique(b * (1 << 32) + f)
+    bptr = np.searchsorted(bfk >> 32, np.arange(len(brick_tile_ptr)))
+    local = np.searchsorted(bfk, b * (1 << 32) + f) - bptr[b]
+    cont = np.zeros(len(t), bool)
+    cont[1:] = (t[1:] == t[:-1]) & (a[1:] == a[:-1]) & (row[1:] == row[:-1])
+    fl = (local | np.where(cont, 0x8000, 0)).astype(np.uint16)
+    seg = t * n_sub + (a >> 5)
+    sub_ptr = np.searchsorted(seg, np.arange(n_tiles * n_sub + 1))
+    import torch as _t
+    valb = _t.from_numpy(val).to(_t.bfloat16).float().numpy()
+    return dict(va=va, fl=fl, val=valb, brick_fasc_ptr=bptr.astype(np.int32), brick_fasc=(bfk & 0xffffffff).astype(np.int32),
+                sub_ptr=sub_ptr.astype(np.int32))
+
+
+@pytest.mark.parametrize("use_ijk", [False, True])
+def test_tc_layout_bit_exact(life, use_ijk):
+    p = synth.config_problem("tiny")
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    idx = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                   p.n_fasc, ijk=p.voxel_ijk if use_ijk else None)
+    info = idx.info()
+    got = {k: v.cpu().numpy() for k, v in life.life_index_export_tiles(idx).items()}
+    m = info["nnz"]
+    exp = expected_tiles(phi, got["tile_vox"], got["brick_tile_ptr"], p.n_voxels, info["n_sub"])
+    np.testing.assert_array_equal(got["sub_ptr"], exp["sub_ptr"])
+    np.testing.assert_array_equal(got["va"][:m].view(np.uint16), exp["va"])
+    np.testing.assert_array_equal(got["val"][:m], exp["val"])
+    np.testing.assert_array_equal(got["brick_fasc_ptr"], exp["brick_fasc_ptr"])
+    np.testing.assert_array_equal(got["brick_fasc"][:info["n_brick_fasc"]], exp["brick_fasc"])
+    np.testing.assert_array_equal(got["fl"][:m].view(np.uint16), exp["fl"])
+    assert sorted(got["brick_order"][:info["n_bricks"]]) == list(range(info["n_bricks"]))
+    if use_ijk:   # every brick's voxels lie in one spatial cube of the stated edge
+        B = info["brick_edge"]
+        for bi in range(info["n_bricks"]):
+            tv = got["tile_vox"][128 * got["brick_tile_ptr"][bi]:128 * got["brick_tile_ptr"][bi + 1]]
+            ijk = p.voxel_ijk[tv[tv >= 0]] // B
+            assert (ijk == ijk[0]).all()
