@@ -412,7 +412,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="paper", choices=["paper", "medium", "tiny"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "paper_small", "medium", "tiny"])
     ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + timed SBB steps inside cudaProfilerStart/Stop, print nothing")

@@ -122,6 +122,12 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     ix->brick_dim = o.brick_dim > 0 ? o.brick_dim : 8;
     cudaGetDevice(&ix->device);
     ix->num_sms = device_sm_count();
+    // The device status word is allocated here, outside any stream capture.
+    if (!dev_status_word()) {
+        delete ix;
+        set_error("life_build_index: cannot allocate the device status word");
+        return LIFE_ENOMEM;
+    }
     // The tensor-core path stores BF16; FP32 storage runs on CUDA cores.
     int algo = o.algo;
     if (algo == LIFE_ALGO_AUTO) algo = o.precision == LIFE_BF16 ? LIFE_ALGO_TC : LIFE_ALGO_SIMT;

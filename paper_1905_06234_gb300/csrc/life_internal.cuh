@@ -140,6 +140,8 @@ struct TileLayout {
     DevBuf brick_fasc;       // int32 [sum] global fascicle id of each brick-local fascicle
     DevBuf brick_order;      // int32 [n_bricks] bricks by decreasing entry count
     DevBuf va;               // uint16 [n_nnz]: row | (atom << 7)
+    DevBuf soff;             // uint16 [n_nnz]: element offset of (row, atom mod 128) in a DSC S chunk
+    DevBuf zoff;             // uint16 [n_nnz]: row * 65 + atom mod 64, the WC Z staging offset
     DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
     DevBuf val;              // bf16 [n_nnz]
 };

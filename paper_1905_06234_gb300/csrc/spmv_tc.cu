@@ -25,8 +25,8 @@ using namespace ptx;
 
 constexpr int SUB = 32;                  // atoms per sub-chunk (offset granularity)
 constexpr uint16_t CONT = 0x8000;        // entry continues the previous entry's (atom, row)
-constexpr uint32_t WAIT_LIMIT = 1u << 24; // polls before a wait gives up (about a second)
-constexpr int ZSTRIDE = 33;              // padded row stride (floats) of the Z staging buffer
+constexpr uint64_t WAIT_LIMIT = 2000000000ull; // ns before a wait gives up
+constexpr int WSUB_MAX = 64;             // atoms per WC Z sub-chunk (32 when shared memory is short)
 
 static int nbits64(int64_t n) {
     if (n <= 1) return 0;
@@ -108,13 +108,16 @@ __global__ void local_fasc_kernel(const uint64_t* __restrict__ key2, const uint3
 // Entry streams in tile order, the continuation flag, and the sub-chunk offsets.
 __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ spay, int64_t m,
                                    int bf, const float* __restrict__ uval, int32_t n_sub, int64_t n_segs,
-                                   uint16_t* __restrict__ va, uint16_t* __restrict__ fl,
-                                   __nv_bfloat16* __restrict__ val, int32_t* __restrict__ sub_ptr) {
+                                   uint16_t* __restrict__ va, uint16_t* __restrict__ soff, uint16_t* __restrict__ zoff,
+                                   uint16_t* __restrict__ fl, __nv_bfloat16* __restrict__ val,
+                                   int32_t* __restrict__ sub_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = skey[j];
         const uint64_t t = k >> (16 + bf);
         const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
         va[j] = (uint16_t)(row | (a << 7));
+        soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) >> 1);
+        zoff[j] = (uint16_t)(row * 65u + (a & 63u));
         val[j] = __float2bfloat16_rn(uval[spay[j]]);
         if (j > 0 && (skey[j - 1] >> bf) == (k >> bf)) fl[j] = (uint16_t)(fl[j] | CONT);
         const int64_t seg = (int64_t)t * n_sub + (a >> 5);
@@ -299,9 +302,13 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     // streams padded to whole 8-entry slots (the kernels load 16 bytes at a time)
     const int64_t m_pad = (m + 7) / 8 * 8 + 8;
     LIFE_TRY(L.va.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.soff.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.zoff.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.fl.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.val.alloc(sizeof(__nv_bfloat16) * m_pad));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.va.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.soff.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.zoff.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.fl.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
     LIFE_TRY(L.sub_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
@@ -312,6 +319,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         LIFE_CHECK_LAUNCH();
         tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
                                                      ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                     L.soff.as<uint16_t>(), L.zoff.as<uint16_t>(),
                                                      L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(),
                                                      L.sub_ptr.as<int32_t>());
         LIFE_CHECK_LAUNCH();
@@ -381,6 +389,8 @@ struct TcArgs {
     const int32_t* brick_fasc;
     const int32_t* brick_order;
     const uint16_t* va;
+    const uint16_t* soff;
+    const uint16_t* zoff;
     const uint16_t* fl;
     const __nv_bfloat16* val;
     const float* D;
@@ -393,6 +403,7 @@ struct TcArgs {
     uint32_t* status;
     int nt, na, np, kp, n_sub, n_bricks, max_fb;
     int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
+    int wsub;            // WC: atoms per Z sub-chunk (32 or 64)
 };
 
 // Brick processed by CTA c in round r (snake over the size-sorted list), or -1.
@@ -418,11 +429,11 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 constexpr int SLOT = 8;
 
 struct EntrySlot {
-    uint4 va, fl, val;
+    uint4 key, fl, val;   // key: S offset (DSC), Z offset or (row, atom) (WC)
 };
 
-__device__ __forceinline__ void load_slot(const TcArgs& A, int base, EntrySlot& s) {
-    s.va = __ldg(reinterpret_cast<const uint4*>(A.va + base));
+__device__ __forceinline__ void load_slot(const uint16_t* key, const TcArgs& A, int base, EntrySlot& s) {
+    s.key = __ldg(reinterpret_cast<const uint4*>(key + base));
     s.fl = __ldg(reinterpret_cast<const uint4*>(A.fl + base));
     s.val = __ldg(reinterpret_cast<const uint4*>(A.val) + (base >> 3));
 }
@@ -454,6 +465,45 @@ __device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int 
     return true;
 }
 
+// dst[i] = src[idx[i]] for i < n, with eight independent loads in flight per thread.
+__device__ __forceinline__ void gather_table(float* dst, const float* __restrict__ src,
+                                             const int32_t* __restrict__ idx, int n, int tid, int nthr) {
+    for (int b0 = 0; b0 < n; b0 += 8 * nthr) {
+        int id[8];
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = b0 + e * nthr + tid;
+            id[e] = i < n ? __ldg(idx + i) : -1;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = id[e] >= 0 ? __ldg(src + id[e]) : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = b0 + e * nthr + tid;
+            if (i < n) dst[i] = v[e];
+        }
+    }
+}
+
+// dst[idx[i]] += tab[i] for every non-zero tab[i], i < n (one atomic per fascicle).
+__device__ __forceinline__ void flush_table(float* dst, const float* tab, const int32_t* __restrict__ idx, int n,
+                                            int tid, int nthr) {
+    for (int b0 = 0; b0 < n; b0 += 8 * nthr) {
+        int id[8];
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = b0 + e * nthr + tid;
+            v[e] = i < n ? tab[i] : 0.0f;
+            id[e] = (i < n && v[e] != 0.0f) ? __ldg(idx + i) : -1;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (id[e] >= 0) atomicAdd(dst + id[e], v[e]);
+    }
+}
+
 // ---------------------------------------------------------------------- DSC
 
 constexpr int DSC_PROD_WARPS = 15;   // 20 warps in all: 5 per SM sub-partition fit 96 registers
@@ -472,40 +522,67 @@ __host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb) {
     return d + DSTAGE * DS_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
-__device__ __forceinline__ void store_s(unsigned char* S, uint32_t va, float s, int c) {
-    const uint32_t row = va & 127u, al = (va >> 7) - (uint32_t)(c * DKC);
-    *reinterpret_cast<__nv_bfloat16*>(S + kmajor_off(row, al, DS_SBO)) = __float2bfloat16_rn(s);
+__device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s) {
+    reinterpret_cast<__nv_bfloat16*>(S)[so] = __float2bfloat16_rn(s);
 }
 
 // S[a, row] for the runs that start inside this slot (a run = entries with the
-// same (atom, row)); a run that goes on past the slot is finished from memory.
-__device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, int base, int beg, int end,
-                                         const float* wl, unsigned char* S, int c) {
-    bool have = false;
-    uint32_t cva = 0;
-    float cs = 0.0f;
+// same (atom, row)).  All 32 lanes of the warp call this together; lane i+1
+// holds the next 8 entries, so a run that goes on past lane i's slot is finished
+// with lane i+1's leading continuation sum (one shuffle).  Only runs that also
+// cross lane i+1's slot, or leave the warp, are finished from memory.
+struct RunState {
+    bool have, head_seen;
+    uint32_t so;
+    float cs, lead;
+};
+
+template <bool CHECK>
+__device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, int end, const float* wl,
+                                         unsigned char* S, RunState& st) {
+    // straight-line code: every lane does the same work for every entry
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
-        const int idx = base + e;
-        if (idx < beg || idx >= end) continue;
+        bool in = true;
+        if (CHECK) {
+            const int idx = base + e;
+            in = idx >= beg && idx < end;
+        }
         const uint32_t f = u16_at(s.fl, e);
-        const float x = bf16_at(s.val, e);
-        if (f & CONT) {
-            if (have) cs = fmaf(x, wl[f & 0x7FFFu], cs);
-        } else {
-            if (have) store_s(S, cva, cs, c);
-            have = true;
-            cva = u16_at(s.va, e);
-            cs = x * wl[f];
-        }
+        const float t = in ? bf16_at(s.val, e) * wl[f & 0x7FFFu] : 0.0f;
+        const bool head = in && !(f & CONT);
+        if (head && st.have) store_s(S, st.so, st.cs);   // the previous run ends here
+        st.lead += (!st.have && !head) ? t : 0.0f;       // continuation of a run owned by the lane before
+        st.cs = head ? t : st.cs + t;
+        st.so = head ? u16_at(s.key, e) : st.so;
+        st.have = st.have || head;
     }
-    if (have) {
-        for (int j = base + SLOT; j < end; ++j) {
-            const uint32_t f = A.fl[j];
-            if (!(f & CONT)) break;
-            cs = fmaf(__bfloat162float(A.val[j]), wl[f & 0x7FFFu], cs);
+    st.head_seen = st.have;
+}
+
+__device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, int base, int beg, int end,
+                                         const float* wl, unsigned char* S, int lane) {
+    RunState st{false, false, 0u, 0.0f, 0.0f};
+    if (base >= beg && base + SLOT <= end) dsc_runs<false>(s, base, beg, end, wl, S, st);
+    else dsc_runs<true>(s, base, beg, end, wl, S, st);
+    // a run may pass through this whole slot into the one after it
+    const int through = (!st.head_seen && base + SLOT < end) ? 1 : 0;
+    const float nlead = __shfl_down_sync(0xffffffffu, st.lead, 1);
+    const int nthrough = __shfl_down_sync(0xffffffffu, through, 1);
+    if (st.have) {
+        const int j0 = base + SLOT;
+        if (j0 < end) {
+            if (lane < 31 && !nthrough) {
+                st.cs += nlead;
+            } else {
+                for (int j = j0; j < end; ++j) {
+                    const uint32_t f = A.fl[j];
+                    if (!(f & CONT)) break;
+                    st.cs += __bfloat162float(A.val[j]) * wl[f & 0x7FFFu];
+                }
+            }
         }
-        store_s(S, cva, cs, c);
+        store_s(S, st.so, st.cs);
     }
 }
 
@@ -569,15 +646,15 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
             int beg = chunk_beg(A, t, 0, spc), end = chunk_beg(A, t, 1, spc);
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
-            EntrySlot cur;
-            if (have) load_slot(A, base, cur);
+            EntrySlot cur{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+            if (have) load_slot(A.soff, A, base, cur);
             bool new_brick = true;
             uint32_t cc = 0;
             for (;;) {
                 if (new_brick) {
                     const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
                     named_bar_sync(1, DSC_PROD_THREADS);
-                    for (int i = tid; i < nfb; i += DSC_PROD_THREADS) wl[i] = __ldg(A.x + A.brick_fasc[fb0 + i]);
+                    gather_table(wl, A.x, A.brick_fasc + fb0, nfb, tid, DSC_PROD_THREADS);
                     named_bar_sync(1, DSC_PROD_THREADS);
                 }
                 const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
@@ -601,22 +678,28 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 }
                 const int nbase = (nbeg & ~7) + tid * SLOT;
                 const bool nhave = nvalid && nbase < nend;
-                EntrySlot nxt;
+                EntrySlot nxt{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
                 bool pf = false;
-                while (have) {
+                // every lane of a warp runs the same number of slot steps (the
+                // warp's first lane decides), so dsc_slot can shuffle
+                const int wbase_off = (tid & ~31) * SLOT;  // this warp's first slot, relative
+                while (__shfl_sync(0xffffffffu, base, 0) < end) {
                     const int b2 = base + DSC_PROD_THREADS * SLOT;
-                    const bool more = b2 < end;
-                    if (more) load_slot(A, b2, nxt);
-                    else if (nhave) {
-                        load_slot(A, nbase, nxt);
+                    const bool more = (b2 - (tid & 31) * SLOT) < end;  // warp-uniform
+                    if (more) {
+                        if (b2 < end) load_slot(A.soff, A, b2, nxt);
+                        else nxt = EntrySlot{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+                    } else if (nhave) {
+                        load_slot(A.soff, A, nbase, nxt);
                         pf = true;
                     }
-                    dsc_slot(A, cur, base, beg, end, wl, S, c);
+                    dsc_slot(A, cur, base, beg, end, wl, S, lane);
                     if (!more) break;
                     cur = nxt;
                     base = b2;
                 }
-                if (!pf && nhave) load_slot(A, nbase, nxt);
+                (void)wbase_off;
+                if (!pf && nhave) load_slot(A.soff, A, nbase, nxt);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full_bar[st]);
@@ -631,7 +714,7 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 new_brick = nnew;
                 base = nbase;
                 have = nhave;
-                if (have) cur = nxt;
+                cur = nxt;  // an empty slot when this lane has none in the next chunk
             }
         }
     } else if (warp < DSC_MMA_WARP) {
@@ -763,14 +846,14 @@ constexpr int WC_MMA_WARP = WC_SCAT_WARPS + WC_LOAD_WARPS;
 constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
 constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
 constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
-constexpr uint32_t ZC_BYTES = TILE_V * ZSTRIDE * 4;
+__host__ __device__ inline uint32_t zc_bytes(int wsub) { return (uint32_t)TILE_V * (wsub + 1) * 4; }
 
-__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb) {
+__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wsub) {
     uint32_t d = (uint32_t)kp * np * 2;
     d = (d + 1023) / 1024 * 1024;
     uint32_t r = (uint32_t)TILE_V * np * 2;
     r = (r + 1023) / 1024 * 1024;
-    return d + r + 2 * ZC_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+    return d + r + 2 * zc_bytes(wsub) + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -779,17 +862,28 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "r"(taddr));
 }
 
-__device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
-                                        int sub) {
+// g_local[f] += val · Z[row, atom] for the entries of one slot.  With 64-atom
+// sub-chunks the key is the precomputed Z offset; with 32-atom ones it is
+// (row, atom) and the offset is computed here.
+template <bool CHECK>
+__device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
+                                          int sub, int wsub) {
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
-        const int idx = base + e;
-        if (idx < beg || idx >= end) continue;
-        const uint32_t v16 = u16_at(s.va, e);
-        const uint32_t row = v16 & 127u, al = (v16 >> 7) - (uint32_t)(SUB * sub);
-        const float p = bf16_at(s.val, e) * Z[row * ZSTRIDE + al];
-        atomicAdd(&gl[u16_at(s.fl, e) & 0x7FFFu], p);
+        if (CHECK) {
+            const int idx = base + e;
+            if (idx < beg || idx >= end) continue;
+        }
+        const uint32_t k = u16_at(s.key, e);
+        const uint32_t zo = wsub == 64 ? k : (k & 127u) * 33u + (k >> 7) - (uint32_t)(32 * sub);
+        atomicAdd(&gl[u16_at(s.fl, e) & 0x7FFFu], bf16_at(s.val, e) * Z[zo]);
     }
+}
+
+__device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
+                                        int sub, int wsub) {
+    if (base >= beg && base + SLOT <= end) wc_slot_t<false>(s, base, beg, end, Z, gl, sub, wsub);
+    else wc_slot_t<true>(s, base, beg, end, Z, gl, sub, wsub);
 }
 
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
@@ -805,8 +899,9 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     const uint32_t r_bytes = align_up((uint32_t)TILE_V * A.np * 2, 1024);
     unsigned char* Dw = smem;
     unsigned char* Rs = smem + d_bytes;
+    const int wsub = A.wsub, zs = wsub + 1;
     float* Zc = reinterpret_cast<float*>(Rs + r_bytes);
-    float* gl = Zc + 2 * TILE_V * ZSTRIDE;
+    float* gl = Zc + 2 * TILE_V * zs;
     const uint32_t SBO_K = (uint32_t)(A.np / 8) * 128u;  // 8-row groups of both operands (K = θ)
 
     // D as the B operand: rows = atoms (N), K = θ; bf16, zero-padded.
@@ -838,17 +933,19 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
 
     if (warp < WC_SCAT_WARPS) {
         // ---------------- Z chunks out of TMEM, then g_local[f] += val·Z[a, row]
-        const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q..; columns 8h .. 8h+7 of each sub-chunk
+        const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q..; columns h*wsub/4 .. of each sub-chunk
+        const int n_ws = A.kp / wsub, sps = wsub / SUB;
         int r = 0;
         const int k0 = brick_at(0, G, cta, A.n_bricks);
         if (k0 >= 0) {
             int brick = A.brick_order[k0], t = A.brick_tile_ptr[brick], sub = 0;
-            int beg = chunk_beg(A, t, 0, 1), end = chunk_beg(A, t, 1, 1);
+            int beg = chunk_beg(A, t, 0, sps), end = chunk_beg(A, t, 1, sps);
+            const uint16_t* wkey = wsub == 64 ? A.zoff : A.va;
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
             EntrySlot cur;
-            if (have) load_slot(A, base, cur);
-            bool new_brick = true, stop = false;
+            if (have) load_slot(wkey, A, base, cur);
+            bool new_brick = true;
             uint32_t tcount = 0, zc = 0;
             int fb0 = 0, nfb = 0;
             for (;;) {
@@ -863,31 +960,37 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                     const bool fail = !warp_wait(&z_full, tcount & 1u, &abort_flag);
                     if (named_bar_or(2, WC_SCAT_THREADS, fail || abort_flag != 0)) {
                         abort_flag = 1;
-                        stop = true;
                         break;
                     }
                     tc_fence_after();
                 }
-                float* Z = Zc + (zc & 1u) * (TILE_V * ZSTRIDE);
-                {
-                    uint32_t r8[8];
-                    tmem_ld8(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(SUB * sub + 8 * h), r8);
+                float* Z = Zc + (zc & 1u) * (TILE_V * zs);
+                if (wsub == 64) {
+                    uint32_t r16[16];
+                    tmem_ld16(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * sub + 16 * h), r16);
                     tmem_ld_wait();
-                    float* zrow = Z + (32 * q + lane) * ZSTRIDE + 8 * h;
+                    float* zrow = Z + (32 * q + lane) * zs + 16 * h;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) zrow[e] = __uint_as_float(r16[e]);
+                } else {
+                    uint32_t r8[8];
+                    tmem_ld8(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * sub + 8 * h), r8);
+                    tmem_ld_wait();
+                    float* zrow = Z + (32 * q + lane) * zs + 8 * h;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) zrow[e] = __uint_as_float(r8[e]);
                 }
-                const bool last_sub = sub == A.n_sub - 1;
+                const bool last_sub = sub == n_ws - 1;
                 if (last_sub) tc_fence_before();
                 named_bar_sync(2, WC_SCAT_THREADS);
                 if (last_sub && tid == 0) mbar_arrive(&z_empty);  // TMEM free for the next tile
                 int nr = r, nbrick = brick, nt = t, nsub = sub;
                 bool nnew = false;
-                const bool nvalid = next_chunk(A, G, cta, A.n_sub, nr, nbrick, nt, nsub, nnew);
+                const bool nvalid = next_chunk(A, G, cta, n_ws, nr, nbrick, nt, nsub, nnew);
                 int nbeg = 0, nend = 0;
                 if (nvalid) {
-                    nbeg = chunk_beg(A, nt, nsub, 1);
-                    nend = chunk_beg(A, nt, nsub + 1, 1);
+                    nbeg = chunk_beg(A, nt, nsub, sps);
+                    nend = chunk_beg(A, nt, nsub + 1, sps);
                 }
                 const int nbase = (nbeg & ~7) + tid * SLOT;
                 const bool nhave = nvalid && nbase < nend;
@@ -896,29 +999,23 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                 while (have) {
                     const int b2 = base + WC_SCAT_THREADS * SLOT;
                     const bool more = b2 < end;
-                    if (more) load_slot(A, b2, nxt);
+                    if (more) load_slot(wkey, A, b2, nxt);
                     else if (nhave) {
-                        load_slot(A, nbase, nxt);
+                        load_slot(wkey, A, nbase, nxt);
                         pf = true;
                     }
-                    wc_slot(cur, base, beg, end, Z, gl, sub);
+                    wc_slot(cur, base, beg, end, Z, gl, sub, wsub);
                     if (!more) break;
                     cur = nxt;
                     base = b2;
                 }
-                if (!pf && nhave) load_slot(A, nbase, nxt);
+                if (!pf && nhave) load_slot(wkey, A, nbase, nxt);
                 ++zc;
                 if (last_sub) ++tcount;
                 if (!nvalid || nnew) {
                     // brick done: flush its fascicle sums to g with one atomic each
-                    if (named_bar_or(2, WC_SCAT_THREADS, abort_flag != 0)) {
-                        stop = true;
-                        break;
-                    }
-                    for (int i = tid; i < nfb; i += WC_SCAT_THREADS) {
-                        const float gv = gl[i];
-                        if (gv != 0.0f) atomicAdd(A.out + A.brick_fasc[fb0 + i], gv);
-                    }
+                    if (named_bar_or(2, WC_SCAT_THREADS, abort_flag != 0)) break;
+                    flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS);
                 }
                 if (!nvalid) break;
                 r = nr;
@@ -932,7 +1029,6 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                 have = nhave;
                 if (have) cur = nxt;
             }
-            (void)stop;
         }
     } else if (warp < WC_MMA_WARP) {
         // ---------------- R tile loader: r[:, v] -> bf16 A operand (rows = voxels, K = θ)
@@ -1056,6 +1152,8 @@ static TcArgs make_args(life_index_s* ix) {
     A.brick_fasc = L.brick_fasc.as<int32_t>();
     A.brick_order = L.brick_order.as<int32_t>();
     A.va = L.va.as<uint16_t>();
+    A.soff = L.soff.as<uint16_t>();
+    A.zoff = L.zoff.as<uint16_t>();
     A.fl = L.fl.as<uint16_t>();
     A.val = L.val.as<__nv_bfloat16>();
     A.nt = ix->nt;
@@ -1106,7 +1204,18 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     A.gate = gate;
     A.gate_mode = gate_mode;
     A.vec4 = (ix->nt % 4 == 0 && (reinterpret_cast<uintptr_t>(r) & 15) == 0) ? 1 : 0;
-    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb);
+    int optin = 0;
+    LIFE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
+    A.wsub = WSUB_MAX;
+    uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wsub);
+    if (smem + 256 > (uint32_t)optin) {
+        A.wsub = 32;
+        smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wsub);
+    }
+    if (smem + 256 > (uint32_t)optin) {
+        set_error("wc_tc: %u bytes of shared memory needed, %d available", smem, optin);
+        return LIFE_ENOTSUP;
+    }
     LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
     wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);

@@ -158,8 +158,11 @@ CONFIGS = {
     "medium": dict(grid=(64, 64, 64), mask=False, n_fasc=50000, steps=(30, 150)),
     "paper": dict(grid=(96, 96, 72), mask=True, n_fasc=500000, steps=(20, 300)),
     "grad": dict(grid=(16, 16, 16), mask=False, n_fasc=2000, steps=(40, 80)),
+    # paper density (entries per voxel and per fascicle) at about a third of the
+    # size: the case profiled with hardware counters
+    "paper_small": dict(grid=(64, 64, 48), mask=True, n_fasc=150000, steps=(20, 300)),
 }
-CONFIG_INDEX = {"tiny": 1, "medium": 2, "paper": 3, "grad": 4, "batched": 5}
+CONFIG_INDEX = {"tiny": 1, "medium": 2, "paper": 3, "grad": 4, "batched": 5, "paper_small": 6}
 
 
 def config_problem(name: str, **overrides) -> Problem:
