@@ -201,7 +201,8 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
                             &idx->atoml.chunk_beg, &idx->atoml.chunk_atom, &idx->atoml.atom_chunk,
                             &idx->tile.tile_vox, &idx->tile.sub_ptr, &idx->tile.brick_tile_ptr,
                             &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
-                            &idx->tile.va, &idx->tile.fl, &idx->tile.val, &idx->red};
+                            &idx->tile.va, &idx->tile.soff, &idx->tile.fl, &idx->tile.val, &idx->tile.wkey,
+                            &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->red};
     int64_t tot = 0;
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;

@@ -99,7 +99,7 @@ struct TmpBuf {
 // ------------------------------------------------------------------ layouts
 
 constexpr int TILE_V = 128;        // voxels per tensor-core tile (MMA M)
-constexpr int MAX_BRICK_FASC = 16384;  // brick-local fascicle table capacity (64 KB of FP32)
+constexpr int MAX_BRICK_FASC = 15872;  // brick-local fascicle table capacity (62 KB of FP32)
 constexpr int RED_SLOTS = 4096;    // per-call FP64 partial-sum slots
 
 // SIMT path: voxel-sorted CSR, (v, a, f) order.
@@ -141,7 +141,11 @@ struct TileLayout {
     DevBuf brick_order;      // int32 [n_bricks] bricks by decreasing entry count
     DevBuf va;               // uint16 [n_nnz]: row | (atom << 7)
     DevBuf soff;             // uint16 [n_nnz]: element offset of (row, atom mod 128) in a DSC S chunk
-    DevBuf zoff;             // uint16 [n_nnz]: row * 65 + atom mod 64, the WC Z staging offset
+    // WC streams, ordered (tile, row quarter, atom, row, fascicle)
+    DevBuf wkey;             // uint16 [n_nnz]: (row mod 32) | (atom mod 32) << 5
+    DevBuf wfl;              // uint16 [n_nnz]: brick-local fascicle
+    DevBuf wval;             // bf16 [n_nnz]
+    DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom sub)
     DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
     DevBuf val;              // bf16 [n_nnz]
 };

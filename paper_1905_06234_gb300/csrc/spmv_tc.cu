@@ -26,7 +26,6 @@ using namespace ptx;
 constexpr int SUB = 32;                  // atoms per sub-chunk (offset granularity)
 constexpr uint16_t CONT = 0x8000;        // entry continues the previous entry's (atom, row)
 constexpr uint64_t WAIT_LIMIT = 2000000000ull; // ns before a wait gives up
-constexpr int WSUB_MAX = 64;             // atoms per WC Z sub-chunk (32 when shared memory is short)
 
 static int nbits64(int64_t n) {
     if (n <= 1) return 0;
@@ -108,7 +107,7 @@ __global__ void local_fasc_kernel(const uint64_t* __restrict__ key2, const uint3
 // Entry streams in tile order, the continuation flag, and the sub-chunk offsets.
 __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ spay, int64_t m,
                                    int bf, const float* __restrict__ uval, int32_t n_sub, int64_t n_segs,
-                                   uint16_t* __restrict__ va, uint16_t* __restrict__ soff, uint16_t* __restrict__ zoff,
+                                   uint16_t* __restrict__ va, uint16_t* __restrict__ soff,
                                    uint16_t* __restrict__ fl, __nv_bfloat16* __restrict__ val,
                                    int32_t* __restrict__ sub_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
@@ -117,7 +116,6 @@ __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint
         const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
         va[j] = (uint16_t)(row | (a << 7));
         soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) >> 1);
-        zoff[j] = (uint16_t)(row * 65u + (a & 63u));
         val[j] = __float2bfloat16_rn(uval[spay[j]]);
         if (j > 0 && (skey[j - 1] >> bf) == (k >> bf)) fl[j] = (uint16_t)(fl[j] | CONT);
         const int64_t seg = (int64_t)t * n_sub + (a >> 5);
@@ -129,6 +127,44 @@ __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint
         for (int64_t q = segp + 1; q <= seg; ++q) sub_ptr[q] = (int32_t)j;
         if (j == m - 1)
             for (int64_t q = seg + 1; q <= n_segs; ++q) sub_ptr[q] = (int32_t)m;
+    }
+}
+
+// WC order: key3 = tile | row quarter | atom | row mod 32 | fascicle (payload:
+// position in the DSC stream)
+__global__ void wc_key_kernel(const uint64_t* __restrict__ skey, int64_t m, int bf, uint64_t* __restrict__ key3,
+                              uint32_t* __restrict__ pay3) {
+    const uint64_t fmask = (1ull << bf) - 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = skey[j];
+        const uint64_t t = k >> (16 + bf), a = (k >> (7 + bf)) & 511u, row = (k >> bf) & 127u;
+        key3[j] = (t << (16 + bf)) | ((row >> 5) << (14 + bf)) | (a << (5 + bf)) | ((row & 31u) << bf) | (k & fmask);
+        pay3[j] = (uint32_t)j;
+    }
+}
+
+__global__ void wc_stream_kernel(const uint64_t* __restrict__ key3, const uint32_t* __restrict__ pay3, int64_t m,
+                                 int bf, const uint16_t* __restrict__ fl, const __nv_bfloat16* __restrict__ val,
+                                 int32_t n_sub, int64_t n_segs, uint16_t* __restrict__ wkey, uint16_t* __restrict__ wfl,
+                                 __nv_bfloat16* __restrict__ wval, int32_t* __restrict__ wseg_ptr) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key3[j];
+        const uint32_t src = pay3[j];
+        const uint64_t t = k >> (16 + bf), q = (k >> (14 + bf)) & 3u, a = (k >> (5 + bf)) & 511u,
+                       r32 = (k >> bf) & 31u;
+        wkey[j] = (uint16_t)(r32 | ((a & 31u) << 5));
+        wfl[j] = (uint16_t)(fl[src] & 0x7FFFu);
+        wval[j] = val[src];
+        const int64_t seg = ((int64_t)t * 4 + (int64_t)q) * n_sub + (int64_t)(a >> 5);
+        int64_t segp = -1;
+        if (j > 0) {
+            const uint64_t kp = key3[j - 1];
+            segp = ((int64_t)(kp >> (16 + bf)) * 4 + (int64_t)((kp >> (14 + bf)) & 3u)) * n_sub +
+                   (int64_t)(((kp >> (5 + bf)) & 511u) >> 5);
+        }
+        for (int64_t q2 = segp + 1; q2 <= seg; ++q2) wseg_ptr[q2] = (int32_t)j;
+        if (j == m - 1)
+            for (int64_t q2 = seg + 1; q2 <= n_segs; ++q2) wseg_ptr[q2] = (int32_t)m;
     }
 }
 
@@ -303,12 +339,10 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     const int64_t m_pad = (m + 7) / 8 * 8 + 8;
     LIFE_TRY(L.va.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.soff.alloc(sizeof(uint16_t) * m_pad));
-    LIFE_TRY(L.zoff.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.fl.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.val.alloc(sizeof(__nv_bfloat16) * m_pad));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.va.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.soff.p, 0, sizeof(uint16_t) * m_pad, s));
-    LIFE_CUDA_TRY(cudaMemsetAsync(L.zoff.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.fl.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
     LIFE_TRY(L.sub_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
@@ -319,12 +353,34 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         LIFE_CHECK_LAUNCH();
         tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
                                                      ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
-                                                     L.soff.as<uint16_t>(), L.zoff.as<uint16_t>(),
+                                                     L.soff.as<uint16_t>(),
                                                      L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(),
                                                      L.sub_ptr.as<int32_t>());
         LIFE_CHECK_LAUNCH();
     } else {
         fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.sub_ptr.as<int32_t>(), n_segs + 1, 0);
+        LIFE_CHECK_LAUNCH();
+    }
+    // WC streams (row quarter major inside each tile)
+    const int64_t n_wsegs = H.n_tiles * 4 * L.n_sub;
+    LIFE_TRY(L.wkey.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.wfl.alloc(sizeof(uint16_t) * m_pad));
+    LIFE_TRY(L.wval.alloc(sizeof(__nv_bfloat16) * m_pad));
+    LIFE_TRY(L.wseg_ptr.alloc(sizeof(int32_t) * (n_wsegs + 1)));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.wkey.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.wfl.p, 0, sizeof(uint16_t) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.wval.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+    if (m > 0) {
+        wc_key_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), m, bf, key2.as<uint64_t>(), pay2.as<uint32_t>());
+        LIFE_CHECK_LAUNCH();
+        LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, nbits64(H.n_tiles) + 16 + bf, s));
+        wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
+                                                   L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub, n_wsegs,
+                                                   L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
+                                                   L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
+        LIFE_CHECK_LAUNCH();
+    } else {
+        fill_kernel<<<grid1d(n_wsegs + 1), 256, 0, s>>>(L.wseg_ptr.as<int32_t>(), n_wsegs + 1, 0);
         LIFE_CHECK_LAUNCH();
     }
     LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
@@ -390,9 +446,12 @@ struct TcArgs {
     const int32_t* brick_order;
     const uint16_t* va;
     const uint16_t* soff;
-    const uint16_t* zoff;
     const uint16_t* fl;
     const __nv_bfloat16* val;
+    const uint16_t* wkey;
+    const uint16_t* wfl;
+    const __nv_bfloat16* wval;
+    const int32_t* wseg_ptr;
     const float* D;
     const float* x;      // DSC: w [Nf];   WC: r [Nθ·Nv]
     const float* b;      // DSC residual or NULL
@@ -403,7 +462,7 @@ struct TcArgs {
     uint32_t* status;
     int nt, na, np, kp, n_sub, n_bricks, max_fb;
     int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
-    int wsub;            // WC: atoms per Z sub-chunk (32 or 64)
+    int wgroups;         // WC: scatter warps per TMEM lane quarter (4, or 2 when shared memory is short)
 };
 
 // Brick processed by CTA c in round r (snake over the size-sorted list), or -1.
@@ -682,10 +741,9 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 bool pf = false;
                 // every lane of a warp runs the same number of slot steps (the
                 // warp's first lane decides), so dsc_slot can shuffle
-                const int wbase_off = (tid & ~31) * SLOT;  // this warp's first slot, relative
                 while (__shfl_sync(0xffffffffu, base, 0) < end) {
                     const int b2 = base + DSC_PROD_THREADS * SLOT;
-                    const bool more = (b2 - (tid & 31) * SLOT) < end;  // warp-uniform
+                    const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;  // warp-uniform
                     if (more) {
                         if (b2 < end) load_slot(A.soff, A, b2, nxt);
                         else nxt = EntrySlot{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
@@ -698,7 +756,6 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                     cur = nxt;
                     base = b2;
                 }
-                (void)wbase_off;
                 if (!pf && nhave) load_slot(A.soff, A, nbase, nxt);
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -839,6 +896,12 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
 }
 
 // ----------------------------------------------------------------------- WC
+//
+// Scatter warps work independently: warp w owns TMEM lane quarter q = w % 4
+// (tile rows 32q .. 32q+31) and every wgroups-th 32-atom sub-chunk, copies that
+// 32x32 block of Z into its own shared-memory tile, and adds val·Z into the
+// brick's fascicle table for the entries of those rows and atoms (the WC stream
+// is ordered by (tile, row quarter, atom, row, fascicle) for exactly this).
 
 constexpr int WC_SCAT_WARPS = 16;
 constexpr int WC_LOAD_WARPS = 3;     // 20 warps in all (see DSC_PROD_WARPS)
@@ -846,28 +909,19 @@ constexpr int WC_MMA_WARP = WC_SCAT_WARPS + WC_LOAD_WARPS;
 constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
 constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
 constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
-__host__ __device__ inline uint32_t zc_bytes(int wsub) { return (uint32_t)TILE_V * (wsub + 1) * 4; }
+constexpr int ZW = 33;                                // row stride (floats) of a warp's Z tile
+constexpr uint32_t ZW_BYTES = 32 * ZW * 4;
 
-__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wsub) {
+__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups) {
     uint32_t d = (uint32_t)kp * np * 2;
     d = (d + 1023) / 1024 * 1024;
     uint32_t r = (uint32_t)TILE_V * np * 2;
     r = (r + 1023) / 1024 * 1024;
-    return d + r + 2 * zc_bytes(wsub) + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+    return d + r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
-
-// g_local[f] += val · Z[row, atom] for the entries of one slot.  With 64-atom
-// sub-chunks the key is the precomputed Z offset; with 32-atom ones it is
-// (row, atom) and the offset is computed here.
 template <bool CHECK>
-__device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
-                                          int sub, int wsub) {
+__device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Zw, float* gl) {
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
         if (CHECK) {
@@ -875,15 +929,18 @@ __device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg,
             if (idx < beg || idx >= end) continue;
         }
         const uint32_t k = u16_at(s.key, e);
-        const uint32_t zo = wsub == 64 ? k : (k & 127u) * 33u + (k >> 7) - (uint32_t)(32 * sub);
-        atomicAdd(&gl[u16_at(s.fl, e) & 0x7FFFu], bf16_at(s.val, e) * Z[zo]);
+        atomicAdd(&gl[u16_at(s.fl, e)], bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)]);
     }
 }
 
-__device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Z, float* gl,
-                                        int sub, int wsub) {
-    if (base >= beg && base + SLOT <= end) wc_slot_t<false>(s, base, beg, end, Z, gl, sub, wsub);
-    else wc_slot_t<true>(s, base, beg, end, Z, gl, sub, wsub);
+__device__ __forceinline__ void wc_load_slot(const TcArgs& A, int base, EntrySlot& s) {
+    s.key = __ldg(reinterpret_cast<const uint4*>(A.wkey + base));
+    s.fl = __ldg(reinterpret_cast<const uint4*>(A.wfl + base));
+    s.val = __ldg(reinterpret_cast<const uint4*>(A.wval) + (base >> 3));
+}
+
+__device__ __forceinline__ int wseg(const TcArgs& A, int t, int q, int s) {
+    return A.wseg_ptr[((int64_t)t * 4 + q) * A.n_sub + s];
 }
 
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
@@ -897,11 +954,11 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t d_bytes = align_up((uint32_t)A.kp * A.np * 2, 1024);
     const uint32_t r_bytes = align_up((uint32_t)TILE_V * A.np * 2, 1024);
+    const int wg = A.wgroups;
     unsigned char* Dw = smem;
     unsigned char* Rs = smem + d_bytes;
-    const int wsub = A.wsub, zs = wsub + 1;
     float* Zc = reinterpret_cast<float*>(Rs + r_bytes);
-    float* gl = Zc + 2 * TILE_V * zs;
+    float* gl = Zc + 4 * wg * (ZW_BYTES / 4);
     const uint32_t SBO_K = (uint32_t)(A.np / 8) * 128u;  // 8-row groups of both operands (K = θ)
 
     // D as the B operand: rows = atoms (N), K = θ; bf16, zero-padded.
@@ -914,7 +971,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         mbar_init(&r_full, WC_LOAD_WARPS);
         mbar_init(&r_empty, 1);
         mbar_init(&z_full, 1);
-        mbar_init(&z_empty, 1);
+        mbar_init(&z_empty, WC_SCAT_WARPS);
         mbar_init(&fin_bar, 1);
         abort_flag = 0;
         never = 0;
@@ -932,103 +989,86 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     const int G = gridDim.x, cta = blockIdx.x;
 
     if (warp < WC_SCAT_WARPS) {
-        // ---------------- Z chunks out of TMEM, then g_local[f] += val·Z[a, row]
-        const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q..; columns h*wsub/4 .. of each sub-chunk
-        const int n_ws = A.kp / wsub, sps = wsub / SUB;
-        int r = 0;
-        const int k0 = brick_at(0, G, cta, A.n_bricks);
-        if (k0 >= 0) {
-            int brick = A.brick_order[k0], t = A.brick_tile_ptr[brick], sub = 0;
-            int beg = chunk_beg(A, t, 0, sps), end = chunk_beg(A, t, 1, sps);
-            const uint16_t* wkey = wsub == 64 ? A.zoff : A.va;
-            int base = (beg & ~7) + tid * SLOT;
-            bool have = base < end;
-            EntrySlot cur;
-            if (have) load_slot(wkey, A, base, cur);
-            bool new_brick = true;
-            uint32_t tcount = 0, zc = 0;
-            int fb0 = 0, nfb = 0;
-            for (;;) {
-                if (new_brick) {
-                    fb0 = A.brick_fasc_ptr[brick];
-                    nfb = A.brick_fasc_ptr[brick + 1] - fb0;
-                    named_bar_sync(2, WC_SCAT_THREADS);
-                    for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
-                    named_bar_sync(2, WC_SCAT_THREADS);
+        const int q = warp & 3, h = warp >> 2;
+        const bool active = h < wg;               // warps beyond wgroups groups only keep step
+        float* Zw = Zc + (active ? (h * 4 + q) : 0) * (ZW_BYTES / 4);
+        uint32_t tcount = 0;
+        bool dead = false;
+        for (int r = 0;; ++r) {
+            const int k = brick_at(r, G, cta, A.n_bricks);
+            if (k < 0) break;
+            const int brick = A.brick_order[k];
+            const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
+            if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
+            for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
+            named_bar_sync(2, WC_SCAT_THREADS);
+            const int t0 = A.brick_tile_ptr[brick], t1 = A.brick_tile_ptr[brick + 1];
+            // this warp's segments in order: (t, s) for t in the brick, s = h, h + wg, ...;
+            // the first slot of the next segment is loaded while the current one is processed
+            const EntrySlot zero{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+            int beg = active ? wseg(A, t0, q, h) : 0, end = active ? wseg(A, t0, q, h + 1) : 0;
+            int base = (beg & ~7) + lane * SLOT;
+            EntrySlot cur = zero;
+            if (active && base < end) wc_load_slot(A, base, cur);
+            for (int t = t0; t < t1 && !dead; ++t, ++tcount) {
+                if (!warp_wait(&z_full, tcount & 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    dead = true;
+                    break;
                 }
-                if (sub == 0) {
-                    const bool fail = !warp_wait(&z_full, tcount & 1u, &abort_flag);
-                    if (named_bar_or(2, WC_SCAT_THREADS, fail || abort_flag != 0)) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    tc_fence_after();
-                }
-                float* Z = Zc + (zc & 1u) * (TILE_V * zs);
-                if (wsub == 64) {
-                    uint32_t r16[16];
-                    tmem_ld16(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * sub + 16 * h), r16);
-                    tmem_ld_wait();
-                    float* zrow = Z + (32 * q + lane) * zs + 16 * h;
+                tc_fence_after();
+                if (active) {
+                    for (int s = h; s < A.n_sub; s += wg) {
+                        uint32_t rr[32];
+                        tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * s), rr);
+                        tmem_ld_wait();
+                        float* zrow = Zw + lane * ZW;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) zrow[e] = __uint_as_float(r16[e]);
-                } else {
-                    uint32_t r8[8];
-                    tmem_ld8(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * sub + 8 * h), r8);
-                    tmem_ld_wait();
-                    float* zrow = Z + (32 * q + lane) * zs + 8 * h;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) zrow[e] = __uint_as_float(r8[e]);
-                }
-                const bool last_sub = sub == n_ws - 1;
-                if (last_sub) tc_fence_before();
-                named_bar_sync(2, WC_SCAT_THREADS);
-                if (last_sub && tid == 0) mbar_arrive(&z_empty);  // TMEM free for the next tile
-                int nr = r, nbrick = brick, nt = t, nsub = sub;
-                bool nnew = false;
-                const bool nvalid = next_chunk(A, G, cta, n_ws, nr, nbrick, nt, nsub, nnew);
-                int nbeg = 0, nend = 0;
-                if (nvalid) {
-                    nbeg = chunk_beg(A, nt, nsub, sps);
-                    nend = chunk_beg(A, nt, nsub + 1, sps);
-                }
-                const int nbase = (nbeg & ~7) + tid * SLOT;
-                const bool nhave = nvalid && nbase < nend;
-                EntrySlot nxt;
-                bool pf = false;
-                while (have) {
-                    const int b2 = base + WC_SCAT_THREADS * SLOT;
-                    const bool more = b2 < end;
-                    if (more) load_slot(wkey, A, b2, nxt);
-                    else if (nhave) {
-                        load_slot(wkey, A, nbase, nxt);
-                        pf = true;
+                        for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                        __syncwarp();
+                        int ns = s + wg, nt = t;
+                        if (ns >= A.n_sub) {
+                            ns = h;
+                            ++nt;
+                        }
+                        const bool nvalid = nt < t1;
+                        const int nbeg = nvalid ? wseg(A, nt, q, ns) : 0, nend = nvalid ? wseg(A, nt, q, ns + 1) : 0;
+                        const int nbase = (nbeg & ~7) + lane * SLOT;
+                        EntrySlot nxt = zero;
+                        bool pf = false;
+                        while (__shfl_sync(0xffffffffu, base, 0) < end) {
+                            const int b2 = base + 32 * SLOT;
+                            const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;
+                            if (more) {
+                                nxt = zero;
+                                if (b2 < end) wc_load_slot(A, b2, nxt);
+                            } else if (nbase < nend) {
+                                wc_load_slot(A, nbase, nxt);
+                                pf = true;
+                            }
+                            if (base >= beg && base + SLOT <= end) wc_slot_t<false>(cur, base, beg, end, Zw, gl);
+                            else wc_slot_t<true>(cur, base, beg, end, Zw, gl);
+                            if (!more) break;
+                            cur = nxt;
+                            base = b2;
+                        }
+                        if (!pf) {
+                            nxt = zero;
+                            if (nbase < nend) wc_load_slot(A, nbase, nxt);
+                        }
+                        cur = nxt;
+                        base = nbase;
+                        beg = nbeg;
+                        end = nend;
+                        __syncwarp();
                     }
-                    wc_slot(cur, base, beg, end, Z, gl, sub, wsub);
-                    if (!more) break;
-                    cur = nxt;
-                    base = b2;
                 }
-                if (!pf && nhave) load_slot(wkey, A, nbase, nxt);
-                ++zc;
-                if (last_sub) ++tcount;
-                if (!nvalid || nnew) {
-                    // brick done: flush its fascicle sums to g with one atomic each
-                    if (named_bar_or(2, WC_SCAT_THREADS, abort_flag != 0)) break;
-                    flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS);
-                }
-                if (!nvalid) break;
-                r = nr;
-                brick = nbrick;
-                t = nt;
-                sub = nsub;
-                beg = nbeg;
-                end = nend;
-                new_brick = nnew;
-                base = nbase;
-                have = nhave;
-                if (have) cur = nxt;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&z_empty);  // this warp is done with the tile's TMEM
             }
+            if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
+            flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS);
         }
     } else if (warp < WC_MMA_WARP) {
         // ---------------- R tile loader: r[:, v] -> bf16 A operand (rows = voxels, K = θ)
@@ -1153,7 +1193,10 @@ static TcArgs make_args(life_index_s* ix) {
     A.brick_order = L.brick_order.as<int32_t>();
     A.va = L.va.as<uint16_t>();
     A.soff = L.soff.as<uint16_t>();
-    A.zoff = L.zoff.as<uint16_t>();
+    A.wkey = L.wkey.as<uint16_t>();
+    A.wfl = L.wfl.as<uint16_t>();
+    A.wval = L.wval.as<__nv_bfloat16>();
+    A.wseg_ptr = L.wseg_ptr.as<int32_t>();
     A.fl = L.fl.as<uint16_t>();
     A.val = L.val.as<__nv_bfloat16>();
     A.nt = ix->nt;
@@ -1206,11 +1249,11 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     A.vec4 = (ix->nt % 4 == 0 && (reinterpret_cast<uintptr_t>(r) & 15) == 0) ? 1 : 0;
     int optin = 0;
     LIFE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
-    A.wsub = WSUB_MAX;
-    uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wsub);
-    if (smem + 256 > (uint32_t)optin) {
-        A.wsub = 32;
-        smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wsub);
+    A.wgroups = 4;
+    uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
+    while (smem + 256 > (uint32_t)optin && A.wgroups > 1) {
+        A.wgroups /= 2;
+        smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
     }
     if (smem + 256 > (uint32_t)optin) {
         set_error("wc_tc: %u bytes of shared memory needed, %d available", smem, optin);
