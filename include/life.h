@@ -54,8 +54,12 @@ enum { LIFE_LAYOUT_VOXEL = 0, LIFE_LAYOUT_FIBER = 1, LIFE_LAYOUT_ATOM = 2 };
 typedef struct {
     int32_t precision;     /* LIFE_FP32 (default) or LIFE_BF16 */
     int32_t algo;          /* LIFE_ALGO_*: SIMT = CUDA-core kernels, TC = tensor-core kernels */
-    int32_t brick_dim;     /* TC path: edge of the cubic voxel brick used for locality (0 = 8) */
-    int32_t reserved[5];   /* must be zero */
+    int32_t brick_dim;     /* TC path: edge of the cubic voxel brick used for locality, 1..64 (0 = 8) */
+    int32_t wc_groups;     /* TC path: WC scatter warp groups per tensor-memory lane quarter, 1, 2 or 4
+                              (0 = 4, or the largest that fits in shared memory) */
+    int32_t autotune;      /* 1 = choose brick_dim and wc_groups by timing candidates on this GPU
+                              (TC path; results cached per problem shape for the process) */
+    int32_t reserved[3];   /* must be zero */
 } life_opts;
 
 typedef struct life_index_s* life_index;
@@ -71,7 +75,10 @@ typedef struct {
     int64_t stream_bytes;  /* bytes of Phi one SpMV streams from memory */
     int64_t n_brick_fasc;  /* TC path: total entries of the brick-local fascicle tables */
     int32_t n_sub;         /* TC path: 32-atom sub-chunks per tile */
-    int32_t brick_edge;    /* TC path: spatial brick edge in voxels (0 = voxel-id groups) */
+    int32_t brick_edge;    /* TC path: spatial brick edge in voxels (0 = runs of voxel ids, when no
+                              coordinates were given) */
+    int32_t wc_groups;     /* TC path: WC scatter groups the next WC launch uses */
+    int32_t tuned;         /* 1 if the autotuner chose brick_edge and wc_groups */
 } life_index_info;
 
 /*
@@ -257,6 +264,90 @@ LIFE_API life_status life_sbbnnls_step(life_index idx, const float* D, const flo
 LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const float* b, float* w,
                                int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
                                void* workspace, void* stream);
+
+/* ------------------------------------------------------- batched SBB-NNLS */
+
+/*
+ * A batch: several independent LiFE problems (one connectome each, same Nθ, Na
+ * and precision) solved together.  The library concatenates them into one
+ * block-diagonal problem, M = diag(M_0, ..., M_{n-1}): problem p's voxels and
+ * fascicles are numbered after those of problems 0..p-1 (life_batch_offsets),
+ * so one DSC or WC launch serves all of them, load-balanced over the SMs, while
+ * each problem keeps its own SBB-NNLS state (Eq. 5-8) and stops on its own.
+ * The problems share the dictionary D (one acquisition scheme and atom model).
+ */
+typedef struct life_batch_s* life_batch;
+
+typedef struct {
+    int32_t n;             /* problems */
+    int32_t algo;          /* LIFE_ALGO_SIMT or LIFE_ALGO_TC: kernels of the combined index */
+    int64_t nnz;           /* merged entries over all problems */
+    int32_t n_voxels;      /* total voxels */
+    int32_t n_fasc;        /* total fascicles */
+    int32_t brick_edge;    /* TC: brick edge of the combined tile layout */
+    int32_t wc_groups;     /* TC: WC scatter groups */
+    int32_t tc_grid;       /* TC: CTAs of one batched SpMV launch */
+    int32_t simt_grid;     /* SIMT: blocks of one batched SpMV launch */
+    int32_t tuned;         /* 1 if the autotuner chose brick_edge and wc_groups */
+    int32_t reserved;
+} life_batch_info;
+
+/*
+ * Builds a batch from n indices (host array of handles), which must agree in Nθ,
+ * Na, precision and device.  The batch copies what it needs: the indices may be
+ * freed afterwards.  opts (host, may be NULL): algo (0 = index 0's), brick_dim
+ * and wc_groups for the combined tile layout (0 = index 0's), autotune = 1 to
+ * choose them by timing (TC path).  Bricks, tiles and SIMT blocks never mix
+ * problems.  Synchronizes `stream`.
+ * Errors: LIFE_EINVAL for n < 1, a null index or mismatched indices;
+ * LIFE_ERANGE when the combined sizes exceed 2^31 - 1.
+ */
+LIFE_API life_status life_batch_create(int32_t n, const life_index* idx, const life_opts* opts, void* stream,
+                                       life_batch* out);
+
+/* Frees the batch (synchronizes the device).  NULL is allowed. */
+LIFE_API life_status life_batch_free(life_batch batch);
+
+/* Sizes and launch facts of a batch (host `out`). */
+LIFE_API life_status life_batch_get_info(life_batch batch, life_batch_info* out);
+
+/* Host arrays [n+1]: first voxel and first fascicle of each problem in the combined numbering. */
+LIFE_API life_status life_batch_offsets(life_batch batch, int32_t* vox_off, int32_t* fasc_off);
+
+/*
+ * The combined block-diagonal index, for DSC / WC on concatenated vectors
+ * (y = diag(M_p) w).  Borrowed: valid until life_batch_free; do not free it.
+ */
+LIFE_API life_status life_batch_index(life_batch batch, life_index* out);
+
+/* Device bytes of the workspace life_batch_solve needs. */
+LIFE_API life_status life_batch_workspace_bytes(life_batch batch, size_t* bytes);
+
+/*
+ * Up to max_iter SBB-NNLS iterations (Eq. 5-8, Algorithm 1) of every problem of
+ * the batch, each from its own w and state, as ONE CUDA graph launch: a
+ * conditional WHILE node whose body is one batched iteration (every launch covers
+ * all problems; a converged problem's work is skipped) and a kernel that decides
+ * on the device whether to iterate again.  Same arithmetic and readings as
+ * life_sbbnnls_step; a problem stops once <g~,g~> = 0 or ‖g~‖ <= tol·‖g~_0‖.
+ *  D          float32 [Nθ·Na], shared by all problems
+ *  b, w       HOST arrays of n DEVICE pointers: b[p] float32 [Nθ·Nv_p], w[p] float32
+ *             [Nf_p] (updated in place)
+ *  st         device array of n states (life_sbb_state_init each, or continue)
+ *  workspace  device, life_batch_workspace_bytes() bytes, 256-byte aligned
+ * Asynchronous; the graph is cached for the same D, st, workspace, tol, rule and
+ * max_iter.  The first call for a configuration must not be inside a stream capture.
+ */
+LIFE_API life_status life_batch_solve(life_batch batch, const float* D, const float* const* b, float* const* w,
+                                      int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
+                                      void* workspace, void* stream);
+
+/*
+ * Runs the autotuner on an existing index (TC path; a no-op otherwise): rebuilds
+ * its tile layout with the brick edge and WC scatter groups that time fastest for
+ * one SBB-NNLS iteration on this GPU.  Synchronizes `stream`.
+ */
+LIFE_API life_status life_index_autotune(life_index idx, void* stream);
 
 /* Checks the device status word every bounded wait in this library writes to;
  * returns LIFE_ETIMEOUT (and clears the word) if one gave up.  Synchronizes. */

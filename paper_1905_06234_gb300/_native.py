@@ -26,7 +26,9 @@ EXPORTS = [
     "life_build_index", "life_index_free", "life_index_get_info", "life_index_export",
     "life_index_export_voxel_streams", "life_index_export_tiles", "life_dsc", "life_wc",
     "life_dsc_grad_D", "life_dsc_grad_D_noalloc", "life_dictionary", "life_dot_f32", "life_sbb_workspace_bytes", "life_sbb_state_init",
-    "life_sbbnnls_step", "life_sbbnnls_solve", "life_check_device_status", "life_last_error", "life_version",
+    "life_sbbnnls_step", "life_sbbnnls_solve", "life_batch_create", "life_batch_free", "life_batch_get_info",
+    "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
+    "life_index_autotune", "life_check_device_status", "life_last_error", "life_version",
 ]
 
 
@@ -38,7 +40,7 @@ class LifeError(RuntimeError):
 
 class life_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("brick_dim", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("wc_groups", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class life_index_info(ctypes.Structure):
@@ -46,7 +48,15 @@ class life_index_info(ctypes.Structure):
                 ("n_atoms", ctypes.c_int32), ("n_voxels", ctypes.c_int32), ("n_fasc", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
                 ("n_bricks", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("stream_bytes", ctypes.c_int64),
-                ("n_brick_fasc", ctypes.c_int64), ("n_sub", ctypes.c_int32), ("brick_edge", ctypes.c_int32)]
+                ("n_brick_fasc", ctypes.c_int64), ("n_sub", ctypes.c_int32), ("brick_edge", ctypes.c_int32),
+                ("wc_groups", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+
+
+class life_batch_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("algo", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("n_voxels", ctypes.c_int32), ("n_fasc", ctypes.c_int32), ("brick_edge", ctypes.c_int32),
+                ("wc_groups", ctypes.c_int32), ("tc_grid", ctypes.c_int32), ("simt_grid", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class life_sbb_state(ctypes.Structure):
@@ -94,6 +104,14 @@ def load(build_if_missing: bool = False):
     L.life_sbb_state_init.argtypes = [P, P]
     L.life_sbbnnls_step.argtypes = [P, P, P, P, P, P, dbl, i32, P]
     L.life_sbbnnls_solve.argtypes = [P, P, P, P, i64, dbl, i32, P, P, P]
+    L.life_batch_create.argtypes = [i32, P, ctypes.POINTER(life_opts), P, ctypes.POINTER(P)]
+    L.life_batch_free.argtypes = [P]
+    L.life_batch_get_info.argtypes = [P, ctypes.POINTER(life_batch_info)]
+    L.life_batch_offsets.argtypes = [P, P, P]
+    L.life_batch_index.argtypes = [P, ctypes.POINTER(P)]
+    L.life_batch_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.life_batch_solve.argtypes = [P, P, P, P, i64, dbl, i32, P, P, P]
+    L.life_index_autotune.argtypes = [P, P]
     L.life_check_device_status.argtypes = [P]
     L.life_last_error.restype = ctypes.c_char_p
     L.life_version.restype = ctypes.c_char_p
@@ -178,7 +196,7 @@ class LifeIndex:
 # ------------------------------------------------------------------ the ABI
 
 def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc, voxel_ijk=None,
-                     precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0) -> LifeIndex:
+                     precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0, wc_groups=0, autotune=False) -> LifeIndex:
     L = load()
     n = int(atom.numel())
     for t, dt, nm in ((atom, torch.int32, "atom"), (voxel, torch.int32, "voxel"), (fasc, torch.int32, "fasc"),
@@ -186,7 +204,8 @@ def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc,
         _need(t, dt, n, nm)
     if voxel_ijk is not None:
         _need(voxel_ijk, torch.int32, 3 * n_voxels, "voxel_ijk")
-    opts = life_opts(precision=int(precision), algo=int(algo), brick_dim=int(brick_dim))
+    opts = life_opts(precision=int(precision), algo=int(algo), brick_dim=int(brick_dim), wc_groups=int(wc_groups),
+                     autotune=1 if autotune else 0)
     h = ctypes.c_void_p()
     _check(L.life_build_index(_ptr(atom), _ptr(voxel), _ptr(fasc), _ptr(val), n, int(n_theta), int(n_atoms),
                               int(n_voxels), int(n_fasc), _ptr(voxel_ijk), ctypes.byref(opts), _stream(),
@@ -347,3 +366,120 @@ def life_check_device_status():
 
 def life_version() -> str:
     return load().life_version().decode()
+
+
+def life_index_autotune(index: LifeIndex):
+    """Re-tunes the tile layout of a tensor-core index on this GPU (no-op otherwise)."""
+    _check(load().life_index_autotune(index.handle, _stream()))
+    return index.info()
+
+
+# ----------------------------------------------------------------- batches
+
+class LifeBatch:
+    """Owner of a life_batch handle: several problems solved together."""
+
+    def __init__(self, handle, lib):
+        self._h = handle
+        self._lib = lib
+        i = self.info()
+        self.n = i["n"]
+        vo = (ctypes.c_int32 * (self.n + 1))()
+        fo = (ctypes.c_int32 * (self.n + 1))()
+        _check(lib.life_batch_offsets(handle, vo, fo))
+        self.vox_off = list(vo)
+        self.fasc_off = list(fo)
+        ih = ctypes.c_void_p()
+        _check(lib.life_batch_index(handle, ctypes.byref(ih)))
+        self.index = _BorrowedIndex(ih, lib, self)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch already freed")
+        return self._h
+
+    def info(self) -> dict:
+        out = life_batch_info()
+        _check(self._lib.life_batch_get_info(self.handle, ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in life_batch_info._fields_ if k != "reserved"}
+
+    def close(self):
+        if self._h is not None:
+            self._lib.life_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _BorrowedIndex(LifeIndex):
+    """The combined index of a batch (owned by the batch, never freed here)."""
+
+    def __init__(self, handle, lib, owner):
+        self._owner = owner
+        super().__init__(handle, lib)
+
+    @property
+    def handle(self):
+        if self._owner._h is None:
+            raise ValueError("batch already freed")
+        return self._h
+
+    def close(self):
+        """Nothing to free: the batch owns the combined index."""
+
+
+def life_batch_create(indices, algo=LIFE_ALGO_AUTO, brick_dim=0, wc_groups=0,
+                      autotune=False) -> LifeBatch:
+    L = load()
+    n = len(indices)
+    arr = (ctypes.c_void_p * n)(*[ix.handle for ix in indices])
+    opts = life_opts(algo=int(algo), brick_dim=int(brick_dim), wc_groups=int(wc_groups),
+                     autotune=1 if autotune else 0)
+    h = ctypes.c_void_p()
+    _check(L.life_batch_create(n, arr, ctypes.byref(opts), _stream(), ctypes.byref(h)))
+    return LifeBatch(h, L)
+
+
+def new_batch_workspace(batch: LifeBatch):
+    n = ctypes.c_size_t()
+    _check(load().life_batch_workspace_bytes(batch.handle, ctypes.byref(n)))
+    return torch.empty(n.value + 256, dtype=torch.uint8, device="cuda")
+
+
+def new_batch_states(n: int):
+    """n device SBB states, initialised (it = 0, alpha = 1)."""
+    st = torch.zeros(n * SBB_STATE_BYTES, dtype=torch.uint8, device="cuda")
+    for p in range(n):
+        _check(load().life_sbb_state_init(ctypes.c_void_p(st.data_ptr() + p * SBB_STATE_BYTES), _stream()))
+    return st
+
+
+def read_batch_states(st, n: int) -> list:
+    raw = st.cpu().numpy().tobytes()
+    out = []
+    for p in range(n):
+        s = life_sbb_state.from_buffer_copy(raw[p * SBB_STATE_BYTES:(p + 1) * SBB_STATE_BYTES])
+        out.append({k: getattr(s, k) for k, _ in life_sbb_state._fields_})
+    return out
+
+
+def life_batch_solve(batch: LifeBatch, D, bs, ws, max_iter, st, workspace, tol=0.0, eq7_on_even=True):
+    """Solves every problem of the batch in one graph launch; ws[p] updated in place."""
+    n = batch.n
+    if len(bs) != n or len(ws) != n:
+        raise ValueError(f"need {n} signals and {n} weight vectors")
+    nt = batch.index.n_theta
+    _need(D, torch.float32, nt * batch.index.n_atoms, "D")
+    for p in range(n):
+        _need(bs[p], torch.float32, nt * (batch.vox_off[p + 1] - batch.vox_off[p]), f"b[{p}]")
+        _need(ws[p], torch.float32, batch.fasc_off[p + 1] - batch.fasc_off[p], f"w[{p}]")
+    _need(st, torch.uint8, n * SBB_STATE_BYTES, "st")
+    bp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in bs])
+    wp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ws])
+    _check(load().life_batch_solve(batch.handle, _ptr(D), bp, wp, int(max_iter), float(tol),
+                                   1 if eq7_on_even else 0, _ptr(st), _aligned(workspace), _stream()))

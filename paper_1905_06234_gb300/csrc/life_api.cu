@@ -45,16 +45,68 @@ life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, f
 static bool use_tc(const life_index_s* ix) { return ix->algo == LIFE_ALGO_TC && ix->tile.built; }
 
 life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
-                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
-    if (use_tc(ix)) return dsc_tc(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
-    return dsc_simt(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s,
+                     const BatchGate& bg) {
+    if (use_tc(ix)) return dsc_tc(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
+    return dsc_simt(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
+}
+
+__global__ void zero_f32_kernel(float* __restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.0f;
 }
 
 life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s) {
-    LIFE_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * (size_t)ix->nf, s));
-    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s);
-    return wc_simt(ix, D, r, g, gate, gate_mode, s);
+                    int gate_mode, cudaStream_t s, const BatchGate& bg) {
+    if (bg.live) {
+        // a kernel rather than a memset, so the batched step is all kernel nodes
+        zero_f32_kernel<<<ix->num_sms * 2, 256, 0, s>>>(g, ix->nf);
+        LIFE_CHECK_LAUNCH();
+    } else {
+        LIFE_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * (size_t)ix->nf, s));
+    }
+    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s, bg);
+    return wc_simt(ix, D, r, g, gate, gate_mode, s, bg);
+}
+
+// Builds every layout of an index whose sizes, precision, brick_dim (and, for a
+// batch, batch.vox_off / batch.vox_group) the caller has set.  algo_req is the
+// requested LIFE_ALGO_*; AUTO picks the tensor-core path for BF16 storage and
+// falls back to the CUDA-core kernels when the tile layout is not supported.
+life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
+                                const float* val, const int32_t* voxel_ijk, int algo_req, cudaStream_t s) {
+    cudaGetDevice(&ix->device);
+    ix->num_sms = device_sm_count();
+    // The device status word is allocated here, outside any stream capture.
+    if (!dev_status_word()) {
+        set_error("life_build_index: cannot allocate the device status word");
+        return LIFE_ENOMEM;
+    }
+    // The tensor-core path stores BF16; FP32 storage runs on CUDA cores.
+    int algo = algo_req;
+    if (algo == LIFE_ALGO_AUTO) algo = ix->precision == LIFE_BF16 ? LIFE_ALGO_TC : LIFE_ALGO_SIMT;
+    if (algo == LIFE_ALGO_TC && ix->precision != LIFE_BF16) {
+        set_error("life_build_index: the tensor-core path stores Phi and D in BF16 (precision = LIFE_BF16)");
+        return LIFE_ENOTSUP;
+    }
+    ix->algo = algo;
+    LIFE_TRY(build_voxel_layout(ix, atom, voxel, fasc, val, s));
+    if (voxel_ijk) {
+        LIFE_TRY(ix->voxel_ijk.alloc(sizeof(int32_t) * 3 * (size_t)ix->nv));
+        LIFE_CUDA_TRY(cudaMemcpyAsync(ix->voxel_ijk.p, voxel_ijk, sizeof(int32_t) * 3 * (size_t)ix->nv,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    if (algo == LIFE_ALGO_TC) {
+        life_status st = build_tile_layout(ix, s);
+        if (st == LIFE_ENOTSUP && algo_req == LIFE_ALGO_AUTO) {
+            ix->algo = LIFE_ALGO_SIMT;  // AUTO falls back to the CUDA-core kernels
+        } else if (st != LIFE_OK) {
+            return st;
+        }
+    }
+    LIFE_TRY(ix->red.alloc(sizeof(double) * 4 * RED_SLOTS));
+    LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    return LIFE_OK;
 }
 
 }  // namespace life
@@ -94,7 +146,7 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     }
     life_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) {
             set_error("life_build_index: reserved option fields must be zero");
             return LIFE_EINVAL;
@@ -105,6 +157,14 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     }
     if (o.algo < LIFE_ALGO_AUTO || o.algo > LIFE_ALGO_TC) {
         set_error("life_build_index: unknown algo %d", o.algo);
+        return LIFE_EINVAL;
+    }
+    if (o.wc_groups != 0 && o.wc_groups != 1 && o.wc_groups != 2 && o.wc_groups != 4) {
+        set_error("life_build_index: wc_groups must be 0, 1, 2 or 4 (got %d)", o.wc_groups);
+        return LIFE_EINVAL;
+    }
+    if (o.brick_dim < 0 || o.brick_dim > 64 || o.autotune < 0 || o.autotune > 1) {
+        set_error("life_build_index: brick_dim must be in [0, 64] and autotune 0 or 1");
         return LIFE_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -120,50 +180,9 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     ix->nnz_raw = nnz;
     ix->precision = o.precision;
     ix->brick_dim = o.brick_dim > 0 ? o.brick_dim : 8;
-    cudaGetDevice(&ix->device);
-    ix->num_sms = device_sm_count();
-    // The device status word is allocated here, outside any stream capture.
-    if (!dev_status_word()) {
-        delete ix;
-        set_error("life_build_index: cannot allocate the device status word");
-        return LIFE_ENOMEM;
-    }
-    // The tensor-core path stores BF16; FP32 storage runs on CUDA cores.
-    int algo = o.algo;
-    if (algo == LIFE_ALGO_AUTO) algo = o.precision == LIFE_BF16 ? LIFE_ALGO_TC : LIFE_ALGO_SIMT;
-    if (algo == LIFE_ALGO_TC && o.precision != LIFE_BF16) {
-        delete ix;
-        set_error("life_build_index: the tensor-core path stores Phi and D in BF16 (precision = LIFE_BF16)");
-        return LIFE_ENOTSUP;
-    }
-    ix->algo = algo;
-    life_status st = build_voxel_layout(ix, atom, voxel, fasc, val, s);
-    if (st == LIFE_OK && voxel_ijk) {
-        st = ix->voxel_ijk.alloc(sizeof(int32_t) * 3 * (size_t)n_voxels);
-        if (st == LIFE_OK) {
-            cudaError_t e = cudaMemcpyAsync(ix->voxel_ijk.p, voxel_ijk, sizeof(int32_t) * 3 * (size_t)n_voxels,
-                                            cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) {
-                set_error("life_build_index: %s", cudaGetErrorString(e));
-                st = LIFE_ECUDA;
-            }
-        }
-    }
-    if (st == LIFE_OK && algo == LIFE_ALGO_TC) {
-        st = build_tile_layout(ix, s);
-        if (st == LIFE_ENOTSUP && o.algo == LIFE_ALGO_AUTO) {
-            ix->algo = LIFE_ALGO_SIMT;  // AUTO falls back to the CUDA-core kernels
-            st = LIFE_OK;
-        }
-    }
-    if (st == LIFE_OK) st = ix->red.alloc(sizeof(double) * 4 * RED_SLOTS);
-    if (st == LIFE_OK) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            set_error("life_build_index: %s", cudaGetErrorString(e));
-            st = LIFE_ECUDA;
-        }
-    }
+    ix->wc_groups = o.wc_groups;
+    life_status st = build_index_layouts(ix, atom, voxel, fasc, val, voxel_ijk, o.algo, s);
+    if (st == LIFE_OK && o.autotune) st = autotune_tc(ix, s);
     if (st != LIFE_OK) {
         delete ix;
         return st;
@@ -194,6 +213,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
     I.n_fasc = idx->nf;
     I.precision = idx->precision;
     I.algo = idx->algo;
+    I.tuned = idx->tuned;
     I.n_tiles = idx->tile.n_tiles;
     I.n_bricks = idx->tile.n_bricks;
     const DevBuf* bufs[] = {&idx->ukey, &idx->uval, &idx->voxel_ijk, &idx->vox.vox_ptr, &idx->vox.atom,
@@ -214,6 +234,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
         I.n_brick_fasc = (int64_t)(idx->tile.brick_fasc.bytes / sizeof(int32_t));
         I.n_sub = idx->tile.n_sub;
         I.brick_edge = idx->tile.brick_edge;
+        I.wc_groups = wc_effective_groups(idx);
     }
     *out = I;
     return LIFE_OK;

@@ -133,6 +133,7 @@ struct TileLayout {
     int32_t n_sub = 0;       // kp / 32
     int32_t max_fb = 0;      // largest brick-local fascicle table
     int32_t brick_edge = 0;  // spatial brick edge used (0 = voxel-id groups)
+    int32_t brick_b = 0;     // brick edge B used (also for voxel-id groups of B^3)
     DevBuf tile_vox;         // int32 [n_tiles * TILE_V] voxel id per tile row (-1 = padding)
     DevBuf sub_ptr;          // int32 [n_tiles * n_sub + 1] entry offsets per (tile, 32-atom sub-chunk)
     DevBuf brick_tile_ptr;   // int32 [n_bricks + 1] tiles of each brick (consecutive)
@@ -150,12 +151,47 @@ struct TileLayout {
     DevBuf val;              // bf16 [n_nnz]
 };
 
+// A block-diagonal index that concatenates several problems (batched solve):
+// problem p owns voxels [vox_off[p], vox_off[p+1]) and fascicles
+// [fasc_off[p], fasc_off[p+1]); no brick, tile or block mixes two problems.
+struct BatchInfo {
+    int32_t n = 0;
+    std::vector<int32_t> vox_off, fasc_off;  // host [n+1]
+    std::vector<int64_t> nnz_off;            // host [n+1] merged entries
+    std::vector<int32_t> vox_group;          // host [Nv] problem of each voxel (tile grouping)
+    DevBuf d_vox_off, d_fasc_off;            // int32 [n+1]
+    DevBuf brick_prob;                       // TC: int32 [n_bricks] problem of each brick
+    int32_t tc_grid = 0;                     // TC: CTAs of a batched SpMV launch
+    int32_t simt_grid = 0;                   // SIMT: blocks of a batched SpMV launch
+    DevBuf blk_prob, blk_rank, blk_count;    // SIMT: int32 [grid], [grid], [n]
+    std::vector<int32_t> part_off;           // host [n+1] per-problem ranges of DSC partial sums
+    DevBuf d_part_off;
+};
+
+// Problem-level gating of a batched launch.  Each work unit (a brick on the TC
+// path, a block on the CUDA-core path) belongs to one problem and runs only while
+// that problem is live; Eq. 8-only work runs only when the problem's current
+// iteration uses Eq. 8.  live == nullptr means an ordinary single-problem launch.
+struct BatchGate {
+    const int32_t* live = nullptr;       // [n] 1 while the problem iterates
+    const life_sbb_state* st = nullptr;  // [n] per-problem states
+    const int32_t* brick_prob = nullptr; // TC: problem of each brick
+    const int32_t* blk_prob = nullptr;   // SIMT: problem of each block
+    const int32_t* blk_rank = nullptr;   // SIMT: rank of a block among its problem's blocks
+    const int32_t* blk_count = nullptr;  // SIMT: blocks of each problem
+    const int32_t* vox_off = nullptr;    // [n+1]
+    int32_t n = 0;
+    int32_t grid = 0;                    // grid of the batched launch
+};
+
 }  // namespace life
 
 struct life_index_s {
     int32_t nt = 0, na = 0, nv = 0, nf = 0;
     int64_t nnz_raw = 0, nnz = 0;
     int32_t precision = LIFE_FP32, algo = LIFE_ALGO_SIMT, brick_dim = 8;
+    int32_t wc_groups = 0;      // TC WC scatter groups (0 = the largest that fits)
+    int32_t tuned = 0;          // 1 once the autotuner chose brick_dim and wc_groups
     int32_t key_bits_v = 0, key_bits_a = 0, key_bits_f = 0;
     int device = 0;
     int num_sms = 0;
@@ -166,6 +202,7 @@ struct life_index_s {
     life::AtomLayout atoml;
     life::TileLayout tile;
     life::DevBuf red;           // double [4 * RED_SLOTS] partial sums
+    life::BatchInfo batch;      // set on the combined index of a batch
     // cached solve graph
     cudaGraphExec_t graph = nullptr;
     const void* graph_key[8] = {nullptr};
@@ -196,17 +233,46 @@ life_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaS
 // `partial` receives one FP64 partial sum per block (n_partial blocks).
 life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
                      double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
-                     cudaStream_t s);
+                     cudaStream_t s, const BatchGate& bg = BatchGate());
 life_status wc_simt(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s);
+                    int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
 life_status grad_D_simt(life_index_s* ix, const float* gy, const float* w, float* gD, cudaStream_t s);
 
 // -------------------------------------------------------------- TC SpMVs
 life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
                    double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
-                   cudaStream_t s);
+                   cudaStream_t s, const BatchGate& bg = BatchGate());
 life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                  int gate_mode, cudaStream_t s);
+                  int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
+
+// ------------------------------------------------------------- dispatch
+// DSC / WC on whichever kernels the index uses (WC zeroes g first).
+life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s,
+                     const BatchGate& bg = BatchGate());
+life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
+                    int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
+life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
+                                const float* val, const int32_t* voxel_ijk, int algo_req, cudaStream_t s);
+// Chooses brick_dim and wc_groups of a tensor-core index by timing candidates
+// (rebuilds the tile layout); a no-op on the CUDA-core path.
+life_status autotune_tc(life_index_s* ix, cudaStream_t s);
+int wc_effective_groups(const life_index_s* ix);
+// Per-problem launch maps of a batch's combined index (after its layouts are built).
+life_status batch_finalize(life_index_s* ix, cudaStream_t s);
+
+// ------------------------------------------------------- batched SBB-NNLS
+// Device workspace of a batched solve (carved from one caller allocation).
+struct BatchWork {
+    float *b, *e, *w, *g, *gt, *u;  // combined signal / residual [Nθ·Nv], weights and gradients [Nf]
+    int32_t* live;                  // [n]
+    int64_t* loops;                 // solve-loop counter
+    double *pe, *pv, *pg, *pu;      // per-problem partial sums
+};
+size_t batch_workspace_bytes(const life_index_s* ix);
+BatchWork batch_carve(const life_index_s* ix, void* ws);
+life_status sbb_enqueue_batch_step(life_index_s* ix, const float* D, life_sbb_state* st, const BatchWork& W,
+                                   double tol, int eq7_on_even, cudaStream_t s);
 
 // ------------------------------------------------------------ reductions
 // Sums `n` partial FP64 values into *out with one block (fixed order).
@@ -219,7 +285,18 @@ enum GateMode : int {
     GATE_NONE = 0,       // always run
     GATE_ACTIVE = 1,     // skip when converged
     GATE_EQ8 = 2,        // skip when converged or this iteration uses Eq. 7
+    GATE_ACTIVE_Y_EQ8 = 3,  // skip when converged; write y only on Eq. 8 iterations
 };
+
+__device__ __forceinline__ bool batch_live(const BatchGate& bg, int p, int mode) {
+    if (!bg.live[p]) return false;
+    if (mode == GATE_EQ8 && bg.st[p].eq != 8) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool batch_writes_y(const BatchGate& bg, int p, int mode) {
+    return mode != GATE_ACTIVE_Y_EQ8 || bg.st[p].eq == 8;
+}
 
 __device__ __forceinline__ bool gate_skip(const life_sbb_state* st, int mode) {
     if (mode == GATE_NONE || st == nullptr) return false;

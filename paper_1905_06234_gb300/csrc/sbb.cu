@@ -269,10 +269,6 @@ static SbbWork carve(const life_index_s* ix, void* ws) {
     return W;
 }
 
-life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
-                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s);
-life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s);
 
 // Enqueues one SBB-NNLS iteration (no host synchronization).
 life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
@@ -300,6 +296,194 @@ life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, f
     sbb_update_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, W.gt, nf, st);
     LIFE_CHECK_LAUNCH();
     (void)ny;
+    return LIFE_OK;
+}
+
+}  // namespace life
+
+// ------------------------------------------------------ batched SBB-NNLS
+//
+// Several independent problems concatenated into one block-diagonal index are
+// iterated together: every launch covers all problems, each problem keeps its
+// own state (Eq. 5-8 decisions, FP64 scalars) and its own per-problem reduction
+// ranges, and work of a problem that has converged is skipped.
+
+namespace life {
+
+constexpr int BATCH_VGX = 32;  // blocks per problem of the batched vector kernels
+
+// live[p] = 1 unless problem p has converged.
+__global__ void batch_live_kernel(int n, const life_sbb_state* __restrict__ st, int32_t* __restrict__ live) {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) live[p] = st[p].converged ? 0 : 1;
+}
+
+// g~ = projected g over problem blockIdx.y's fascicles; per-block Σ g~².
+__global__ void batch_project_kernel(const float* __restrict__ w, const float* __restrict__ g,
+                                     float* __restrict__ gt, const int32_t* __restrict__ fasc_off,
+                                     double* __restrict__ pg, const int32_t* __restrict__ live) {
+    const int p = blockIdx.y;
+    if (!live[p]) return;
+    const int64_t f1 = fasc_off[p + 1];
+    double s = 0.0;
+    for (int64_t i = fasc_off[p] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < f1;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float v = (w[i] == 0.0f && gi > 0.0f) ? 0.0f : gi;
+        gt[i] = v;
+        s += (double)v * (double)v;
+    }
+    const double t = block_reduce(s);
+    if (threadIdx.x == 0) pg[(int64_t)p * gridDim.x + blockIdx.x] = t;
+}
+
+// Per problem (one block each): obj, <g~,g~>, the stopping test and the step rule.
+__global__ void batch_scalars1_kernel(life_sbb_state* st_all, int32_t* live, const double* __restrict__ pe,
+                                      const int32_t* __restrict__ part_off, const double* __restrict__ pg,
+                                      int vgx, double tol, int eq7_on_even) {
+    const int p = blockIdx.x;
+    if (!live[p]) return;
+    life_sbb_state* st = st_all + p;
+    const double ee = sum_partials(pe + part_off[p], part_off[p + 1] - part_off[p]);
+    __syncthreads();
+    const double gg = sum_partials(pg + (int64_t)p * vgx, vgx);
+    if (threadIdx.x != 0) return;
+    st->obj = 0.5 * ee;
+    st->gg = gg;
+    if (st->it == 0) st->gg0 = gg;
+    if (gg == 0.0 || sqrt(gg) <= tol * sqrt(st->gg0)) {
+        st->converged = 1;
+        st->eq = 0;
+        live[p] = 0;
+        return;
+    }
+    const bool even = (st->it & 1) == 0;
+    st->eq = (eq7_on_even ? even : !even) ? 7 : 8;
+}
+
+// Σ v''² over problem blockIdx.y's fascicles (Eq. 8 iterations only).
+__global__ void batch_sumsq_kernel(const float* __restrict__ u, const int32_t* __restrict__ fasc_off,
+                                   double* __restrict__ pu, const int32_t* __restrict__ live,
+                                   const life_sbb_state* __restrict__ st) {
+    const int p = blockIdx.y;
+    if (!live[p] || st[p].eq != 8) return;
+    const int64_t f1 = fasc_off[p + 1];
+    double s = 0.0;
+    for (int64_t i = fasc_off[p] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < f1;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = u[i];
+        s += v * v;
+    }
+    const double t = block_reduce(s);
+    if (threadIdx.x == 0) pu[(int64_t)p * gridDim.x + blockIdx.x] = t;
+}
+
+// Per problem: <v',v'>, <v'',v''>, the step size (Eq. 7 or Eq. 8) and the count.
+__global__ void batch_scalars2_kernel(life_sbb_state* st_all, const int32_t* __restrict__ live,
+                                      const double* __restrict__ pv, const int32_t* __restrict__ part_off,
+                                      const double* __restrict__ pu, int vgx) {
+    const int p = blockIdx.x;
+    if (!live[p]) return;
+    life_sbb_state* st = st_all + p;
+    const double vv = sum_partials(pv + part_off[p], part_off[p + 1] - part_off[p]);
+    __syncthreads();
+    double uu = 0.0;
+    if (st->eq == 8) uu = sum_partials(pu + (int64_t)p * vgx, vgx);
+    if (threadIdx.x != 0) return;
+    double alpha = st->alpha;
+    if (st->eq == 7) {
+        if (vv > 0.0) alpha = st->gg / vv;   // Eq. 7
+    } else {
+        if (uu > 0.0) alpha = vv / uu;       // Eq. 8
+    }
+    st->vv = vv;
+    st->uu = uu;
+    st->alpha = alpha;
+    st->it += 1;
+}
+
+// w = [w − alpha_p g~]_+ over problem blockIdx.y's fascicles (Eq. 5).
+__global__ void batch_update_kernel(float* __restrict__ w, const float* __restrict__ gt,
+                                    const int32_t* __restrict__ fasc_off, const life_sbb_state* __restrict__ st,
+                                    const int32_t* __restrict__ live) {
+    const int p = blockIdx.y;
+    if (!live[p]) return;
+    const float alpha = (float)st[p].alpha;
+    const int64_t f1 = fasc_off[p + 1];
+    for (int64_t i = fasc_off[p] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < f1;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = fmaf(-alpha, gt[i], w[i]);
+        w[i] = x > 0.0f ? x : 0.0f;
+    }
+}
+
+size_t batch_workspace_bytes(const life_index_s* ix) {
+    const BatchInfo& bi = ix->batch;
+    const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf, n = bi.n;
+    const size_t np = std::max<size_t>(bi.part_off.empty() ? 1 : bi.part_off.back(), 1);
+    return 2 * align256(ny * 4) + 4 * align256(nf * 4) + align256(n * 4) + align256(8) + 2 * align256(np * 8) +
+           2 * align256(n * BATCH_VGX * 8);
+}
+
+BatchWork batch_carve(const life_index_s* ix, void* ws) {
+    const BatchInfo& bi = ix->batch;
+    const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf, n = bi.n;
+    const size_t np = std::max<size_t>(bi.part_off.empty() ? 1 : bi.part_off.back(), 1);
+    char* p = static_cast<char*>(ws);
+    BatchWork W;
+    W.b = reinterpret_cast<float*>(p); p += align256(ny * 4);
+    W.e = reinterpret_cast<float*>(p); p += align256(ny * 4);
+    W.w = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.g = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.gt = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.u = reinterpret_cast<float*>(p); p += align256(nf * 4);
+    W.live = reinterpret_cast<int32_t*>(p); p += align256(n * 4);
+    W.loops = reinterpret_cast<int64_t*>(p); p += align256(8);
+    W.pe = reinterpret_cast<double*>(p); p += align256(np * 8);
+    W.pv = reinterpret_cast<double*>(p); p += align256(np * 8);
+    W.pg = reinterpret_cast<double*>(p); p += align256(n * BATCH_VGX * 8);
+    W.pu = reinterpret_cast<double*>(p);
+    return W;
+}
+
+// Enqueues one SBB-NNLS iteration of every live problem of a batch (no host
+// synchronization, no allocation: it can be captured into a conditional graph body).
+life_status sbb_enqueue_batch_step(life_index_s* ix, const float* D, life_sbb_state* st, const BatchWork& W,
+                                   double tol, int eq7_on_even, cudaStream_t s) {
+    const BatchInfo& bi = ix->batch;
+    const int n = bi.n;
+    BatchGate bg;
+    bg.live = W.live;
+    bg.st = st;
+    bg.brick_prob = bi.brick_prob.as<int32_t>();
+    bg.blk_prob = bi.blk_prob.as<int32_t>();
+    bg.blk_rank = bi.blk_rank.as<int32_t>();
+    bg.blk_count = bi.blk_count.as<int32_t>();
+    bg.vox_off = bi.d_vox_off.as<int32_t>();
+    bg.n = n;
+    bg.grid = ix->algo == LIFE_ALGO_TC && ix->tile.built ? bi.tc_grid : bi.simt_grid;
+    const int32_t* fasc_off = bi.d_fasc_off.as<int32_t>();
+    const int32_t* part_off = bi.d_part_off.as<int32_t>();
+    const dim3 vgrid(BATCH_VGX, n);
+    batch_live_kernel<<<1, RED_THREADS, 0, s>>>(n, st, W.live);
+    LIFE_CHECK_LAUNCH();
+    // e = M w − b, Σ e² per problem
+    LIFE_TRY(spmv_dsc(ix, D, W.w, W.b, W.e, W.pe, nullptr, st, GATE_ACTIVE, s, bg));
+    // g = M^T e
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s, bg));
+    batch_project_kernel<<<vgrid, RED_THREADS, 0, s>>>(W.w, W.g, W.gt, fasc_off, W.pg, W.live);
+    LIFE_CHECK_LAUNCH();
+    batch_scalars1_kernel<<<n, RED_THREADS, 0, s>>>(st, W.live, W.pe, part_off, W.pg, BATCH_VGX, tol, eq7_on_even);
+    LIFE_CHECK_LAUNCH();
+    // v' = M g~ (stored on Eq. 8 iterations), Σ v'²
+    LIFE_TRY(spmv_dsc(ix, D, W.gt, nullptr, W.e, W.pv, nullptr, st, GATE_ACTIVE_Y_EQ8, s, bg));
+    // v'' = M^T v', Σ v''² (Eq. 8 iterations)
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s, bg));
+    batch_sumsq_kernel<<<vgrid, RED_THREADS, 0, s>>>(W.u, fasc_off, W.pu, W.live, st);
+    LIFE_CHECK_LAUNCH();
+    batch_scalars2_kernel<<<n, RED_THREADS, 0, s>>>(st, W.live, W.pv, part_off, W.pu, BATCH_VGX);
+    LIFE_CHECK_LAUNCH();
+    batch_update_kernel<<<vgrid, RED_THREADS, 0, s>>>(W.w, W.gt, fasc_off, st, W.live);
+    LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
 

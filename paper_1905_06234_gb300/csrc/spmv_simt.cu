@@ -53,21 +53,36 @@ __global__ void __launch_bounds__(SIMT_THREADS)
 dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
                 const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D,
                 int nt, int na, int nv, const float* __restrict__ w, const float* __restrict__ b,
-                float* __restrict__ y, double* __restrict__ partial, const life_sbb_state* gate, int gate_mode) {
+                float* __restrict__ y, double* __restrict__ partial, const life_sbb_state* gate, int gate_mode,
+                const BatchGate bg) {
     extern __shared__ float Ds[];
     __shared__ double red[32];
-    if (gate_skip(gate, gate_mode)) return;
     bool write_y = y != nullptr;
-    if (gate && gate_mode == 3 && gate->eq != 8) write_y = false;
+    int v0, vstep, vend;
+    if (bg.live) {
+        // batched launch: this block serves one problem's voxel range
+        const int p = bg.blk_prob[blockIdx.x];
+        if (!batch_live(bg, p, gate_mode)) return;
+        write_y = write_y && batch_writes_y(bg, p, gate_mode);
+        const int wpb = blockDim.x >> 5;
+        v0 = bg.vox_off[p] + bg.blk_rank[blockIdx.x] * wpb + (threadIdx.x >> 5);
+        vstep = bg.blk_count[p] * wpb;
+        vend = bg.vox_off[p + 1];
+    } else {
+        if (gate_skip(gate, gate_mode)) return;
+        if (gate && gate_mode == GATE_ACTIVE_Y_EQ8 && gate->eq != 8) write_y = false;
+        v0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        vstep = (gridDim.x * blockDim.x) >> 5;
+        vend = nv;
+    }
     constexpr int NTP = NTW * 32;
     if (SMEM_D) {
         stage_D<NTW>(Ds, D, nt, na);
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
     double sq = 0.0;
-    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+    for (int v = v0; v < vend; v += vstep) {
         float acc[NTW];
 #pragma unroll
         for (int q = 0; q < NTW; ++q) acc[q] = 0.0f;
@@ -142,17 +157,29 @@ __global__ void __launch_bounds__(SIMT_THREADS)
 wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
                const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D, int nt,
                int na, int nv, const float* __restrict__ r, float* __restrict__ g, const life_sbb_state* gate,
-               int gate_mode) {
+               int gate_mode, const BatchGate bg) {
     extern __shared__ float Ds[];
-    if (gate_skip(gate, gate_mode)) return;
+    int v0, vstep, vend;
+    if (bg.live) {
+        const int p = bg.blk_prob[blockIdx.x];
+        if (!batch_live(bg, p, gate_mode)) return;
+        const int wpb = blockDim.x >> 5;
+        v0 = bg.vox_off[p] + bg.blk_rank[blockIdx.x] * wpb + (threadIdx.x >> 5);
+        vstep = bg.blk_count[p] * wpb;
+        vend = bg.vox_off[p + 1];
+    } else {
+        if (gate_skip(gate, gate_mode)) return;
+        v0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        vstep = (gridDim.x * blockDim.x) >> 5;
+        vend = nv;
+    }
     constexpr int NTP = NTW * 32;
     if (SMEM_D) {
         stage_D<NTW>(Ds, D, nt, na);
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+    for (int v = v0; v < vend; v += vstep) {
         const int beg = vox_ptr[v], end = vox_ptr[v + 1];
         if (beg == end) continue;
         float rr[NTW];
@@ -250,14 +277,14 @@ __global__ void graddD_reduce_kernel(const int32_t* __restrict__ atom_chunk, int
 template <int NTW, bool SMEM, class VT>
 static life_status launch_dsc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
                               double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
-                              cudaStream_t s) {
+                              cudaStream_t s, const BatchGate& bg) {
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
     auto kern = dsc_simt_kernel<NTW, SMEM, VT>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = ix->num_sms;
+    const int grid = bg.live ? bg.grid : ix->num_sms;
     kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
                                           ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p), D,
-                                          ix->nt, ix->na, ix->nv, w, b, y, partial, gate, gate_mode);
+                                          ix->nt, ix->na, ix->nv, w, b, y, partial, gate, gate_mode, bg);
     LIFE_CHECK_LAUNCH();
     if (n_partial) *n_partial = grid;
     return LIFE_OK;
@@ -265,41 +292,42 @@ static life_status launch_dsc(life_index_s* ix, const float* D, const float* w, 
 
 template <int NTW, bool SMEM, class VT>
 static life_status launch_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                             int gate_mode, cudaStream_t s) {
+                             int gate_mode, cudaStream_t s, const BatchGate& bg) {
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
     auto kern = wc_simt_kernel<NTW, SMEM, VT>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<ix->num_sms, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
-                                                 ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p),
-                                                 D, ix->nt, ix->na, ix->nv, r, g, gate, gate_mode);
+    const int grid = bg.live ? bg.grid : ix->num_sms;
+    kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
+                                          ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p), D,
+                                          ix->nt, ix->na, ix->nv, r, g, gate, gate_mode, bg);
     LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
 
 life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
-                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
+                     int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s, const BatchGate& bg) {
     const int ntw = (ix->nt + 31) / 32;
     const bool smem = (size_t)ix->na * ntw * 32 * sizeof(float) <= SIMT_SMEM_LIMIT;
     const bool bf = ix->precision == LIFE_BF16;
     LIFE_NTW_SWITCH(ntw, {
-        if (smem && bf) return launch_dsc<NTW, true, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
-        if (smem) return launch_dsc<NTW, true, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
-        if (bf) return launch_dsc<NTW, false, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
-        return launch_dsc<NTW, false, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s);
+        if (smem && bf) return launch_dsc<NTW, true, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
+        if (smem) return launch_dsc<NTW, true, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
+        if (bf) return launch_dsc<NTW, false, __nv_bfloat16>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
+        return launch_dsc<NTW, false, float>(ix, D, w, b, y, partial, n_partial, gate, gate_mode, s, bg);
     });
     return LIFE_OK;
 }
 
 life_status wc_simt(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s) {
+                    int gate_mode, cudaStream_t s, const BatchGate& bg) {
     const int ntw = (ix->nt + 31) / 32;
     const bool smem = (size_t)ix->na * ntw * 32 * sizeof(float) <= SIMT_SMEM_LIMIT;
     const bool bf = ix->precision == LIFE_BF16;
     LIFE_NTW_SWITCH(ntw, {
-        if (smem && bf) return launch_wc<NTW, true, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s);
-        if (smem) return launch_wc<NTW, true, float>(ix, D, r, g, gate, gate_mode, s);
-        if (bf) return launch_wc<NTW, false, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s);
-        return launch_wc<NTW, false, float>(ix, D, r, g, gate, gate_mode, s);
+        if (smem && bf) return launch_wc<NTW, true, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s, bg);
+        if (smem) return launch_wc<NTW, true, float>(ix, D, r, g, gate, gate_mode, s, bg);
+        if (bf) return launch_wc<NTW, false, __nv_bfloat16>(ix, D, r, g, gate, gate_mode, s, bg);
+        return launch_wc<NTW, false, float>(ix, D, r, g, gate, gate_mode, s, bg);
     });
     return LIFE_OK;
 }

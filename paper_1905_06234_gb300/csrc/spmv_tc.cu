@@ -179,8 +179,11 @@ struct HostTiles {
 
 // Groups voxels into bricks (spatial B^3 cubes when coordinates are known,
 // else runs of B^3 consecutive voxel ids) and each brick into 128-voxel tiles.
-static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, int B, HostTiles& H) {
+// For the combined index of a batch, bricks never mix problems: the problem is
+// the leading part of the brick key, and voxel-id runs restart at each problem.
+static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, int B, const BatchInfo& bi, HostTiles& H) {
     std::vector<int64_t> bkey(nv);
+    const bool grouped = !bi.vox_group.empty();
     if (!ijk.empty()) {
         int32_t mx[3] = {0, 0, 0};
         for (int32_t v = 0; v < nv; ++v)
@@ -190,8 +193,11 @@ static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, int B, Hos
             bkey[v] = ((int64_t)(ijk[3 * v + 2] / B) * nby + ijk[3 * v + 1] / B) * nbx + ijk[3 * v] / B;
     } else {
         const int64_t bs = (int64_t)B * B * B;
-        for (int32_t v = 0; v < nv; ++v) bkey[v] = v / bs;
+        for (int32_t v = 0; v < nv; ++v)
+            bkey[v] = (grouped ? v - bi.vox_off[bi.vox_group[v]] : v) / bs;
     }
+    if (grouped)
+        for (int32_t v = 0; v < nv; ++v) bkey[v] |= (int64_t)bi.vox_group[v] << 40;
     std::vector<int32_t> order(nv);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bkey[x] < bkey[y]; });
@@ -273,7 +279,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     const int B0 = std::max(2, ix->brick_dim);
     for (int B : {B0, B0 * 3 / 4, B0 / 2, B0 / 4}) {
         if (B < 1) continue;
-        assign_tiles(ix->nv, ijk, B, H);
+        assign_tiles(ix->nv, ijk, B, ix->batch, H);
         LIFE_TRY(upload(d_vox_tile, H.vox_tile, s));
         LIFE_TRY(upload(d_vox_row, H.vox_row, s));
         LIFE_TRY(upload(d_tile_brick, H.tile_brick, s));
@@ -321,6 +327,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         for (int64_t b = 0; b < H.n_bricks; ++b) mx = std::max(mx, hbptr[b + 1] - hbptr[b]);
         L.max_fb = mx;
         L.brick_edge = ijk.empty() ? 0 : B;
+        L.brick_b = B;
         if (mx <= MAX_BRICK_FASC) {
             ok = true;
             break;
@@ -334,6 +341,14 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     L.n_tiles = H.n_tiles;
     L.n_bricks = H.n_bricks;
     L.n_nnz = m;
+    if (!ix->batch.vox_group.empty()) {
+        // problem of each brick (every voxel of a brick belongs to one problem; row 0
+        // of a brick's first tile is always a voxel)
+        std::vector<int32_t> bp(H.n_bricks);
+        for (int64_t b = 0; b < H.n_bricks; ++b)
+            bp[b] = ix->batch.vox_group[H.tile_vox[(size_t)H.brick_tile_ptr[b] * TILE_V]];
+        LIFE_TRY(upload(ix->batch.brick_prob, bp, s));
+    }
     const int64_t n_segs = H.n_tiles * L.n_sub;
     // streams padded to whole 8-entry slots (the kernels load 16 bytes at a time)
     const int64_t m_pad = (m + 7) / 8 * 8 + 8;
@@ -463,12 +478,26 @@ struct TcArgs {
     int nt, na, np, kp, n_sub, n_bricks, max_fb;
     int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
     int wgroups;         // WC: scatter warps per TMEM lane quarter (4, or 2 when shared memory is short)
+    BatchGate bg;        // batched launch: bricks of problems that are not live are skipped, and DSC
+                         // partial sums go to partial[(p * grid + cta) * DSC_EPI_WARPS + epilogue warp]
 };
 
 // Brick processed by CTA c in round r (snake over the size-sorted list), or -1.
 __device__ __forceinline__ int brick_at(int r, int G, int c, int nb) {
     const int k = r * G + ((r & 1) ? (G - 1 - c) : c);
     return k < nb ? k : -1;
+}
+
+// The first brick of this CTA at round >= r whose problem is live (r is advanced
+// to its round); -1 when none is left.  Every role of a CTA walks the same
+// sequence, since the problem states do not change during a launch.
+__device__ __forceinline__ int live_brick(const TcArgs& A, int G, int cta, int& r) {
+    for (;; ++r) {
+        const int k = brick_at(r, G, cta, A.n_bricks);
+        if (k < 0) return -1;
+        const int brick = A.brick_order[k];
+        if (!A.bg.live || batch_live(A.bg, A.bg.brick_prob[brick], A.gate_mode)) return brick;
+    }
 }
 
 __device__ __forceinline__ uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -516,9 +545,9 @@ __device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int 
     c = 0;
     if (++t < A.brick_tile_ptr[brick + 1]) return true;
     ++r;
-    const int k = brick_at(r, G, cta, A.n_bricks);
-    if (k < 0) return false;
-    brick = A.brick_order[k];
+    const int nb = live_brick(A, G, cta, r);
+    if (nb < 0) return false;
+    brick = nb;
     t = A.brick_tile_ptr[brick];
     new_brick = true;
     return true;
@@ -645,14 +674,23 @@ __device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, in
     }
 }
 
+// Batched launch: adds this epilogue warp's Σ out² for problem p to its own slot
+// (one writer per slot, so the sum is deterministic) and restarts the sum.
+__device__ __forceinline__ void dsc_flush_sq(const TcArgs& A, double& sq, int p, int G, int cta, int q, int lane) {
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0 && A.partial) A.partial[((int64_t)p * G + cta) * DSC_EPI_WARPS + q] += sq;
+    sq = 0.0;
+}
+
 __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, never;
     __shared__ double red[DSC_EPI_WARPS];
-    if (gate_skip(A.gate, A.gate_mode)) return;
-    const bool write_y = A.out != nullptr && !(A.gate && A.gate_mode == 3 && A.gate->eq != 8);
+    if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
+    const bool write_y = A.out != nullptr && (A.bg.live || !(A.gate && A.gate_mode == GATE_ACTIVE_Y_EQ8 &&
+                                                               A.gate->eq != 8));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -699,9 +737,9 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
     if (warp < DSC_PROD_WARPS) {
         // ---------------- producers: S[a, row] = Σ val·w for one 128-atom chunk
         int r = 0;
-        const int k0 = brick_at(0, G, cta, A.n_bricks);
-        if (k0 >= 0) {
-            int brick = A.brick_order[k0], t = A.brick_tile_ptr[brick], c = 0;
+        const int b0 = live_brick(A, G, cta, r);
+        if (b0 >= 0) {
+            int brick = b0, t = A.brick_tile_ptr[brick], c = 0;
             int beg = chunk_beg(A, t, 0, spc), end = chunk_beg(A, t, 1, spc);
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
@@ -781,10 +819,21 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         const bool vec = A.vec4 != 0;
         uint32_t tcount = 0;
         bool stop = false;
+        int cur_p = -1;  // batched launch: problem whose Σ out² is being accumulated
+        if (A.bg.live && lane == 0 && A.partial)
+            for (int p = 0; p < A.bg.n; ++p) A.partial[((int64_t)p * G + cta) * DSC_EPI_WARPS + q] = 0.0;
         for (int r = 0; !stop; ++r) {
-            const int k = brick_at(r, G, cta, A.n_bricks);
-            if (k < 0) break;
-            const int brick = A.brick_order[k];
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
+            bool wy = write_y;
+            if (A.bg.live) {
+                const int p = A.bg.brick_prob[brick];
+                wy = write_y && batch_writes_y(A.bg, p, A.gate_mode);
+                if (p != cur_p) {
+                    if (cur_p >= 0) dsc_flush_sq(A, sq, cur_p, G, cta, q, lane);
+                    cur_p = p;
+                }
+            }
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
                 const uint32_t ab = tcount & 1u, aph = (tcount >> 1) & 1u;
                 if (!warp_wait(&acc_full[ab], aph, &abort_flag)) {
@@ -822,7 +871,7 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                                 yv.z -= bv.z;
                                 yv.w -= bv.w;
                             }
-                            if (write_y) *reinterpret_cast<float4*>(A.out + o + e) = yv;
+                            if (wy) *reinterpret_cast<float4*>(A.out + o + e) = yv;
                             sqf += yv.x * yv.x + yv.y * yv.y + yv.z * yv.z + yv.w * yv.w;
                         }
                     } else {
@@ -830,7 +879,7 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                             if (j + e < A.nt) {
                                 float y = __uint_as_float(rr[e]);
                                 if (A.b) y -= A.b[o + e];
-                                if (write_y) A.out[o + e] = y;
+                                if (wy) A.out[o + e] = y;
                                 sqf += y * y;
                             }
                         }
@@ -843,8 +892,12 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 ++tcount;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) red[q] = sq;
+        if (A.bg.live) {
+            if (cur_p >= 0) dsc_flush_sq(A, sq, cur_p, G, cta, q, lane);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) red[q] = sq;
+        }
     } else if (lane == 0) {
         // ---------------- MMA issuer: Yᵀ[128 x np] = S[128 x kp] · Dᵀ
         const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)A.np);
@@ -852,9 +905,8 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         uint32_t cc = 0, tcount = 0;
         bool stop = false;
         for (int r = 0; !stop; ++r) {
-            const int k = brick_at(r, G, cta, A.n_bricks);
-            if (k < 0) break;
-            const int brick = A.brick_order[k];
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1] && !stop; ++t) {
                 const uint32_t ab = tcount & 1u, aph = (tcount >> 1) & 1u;
                 if (!mbar_wait(&acc_empty[ab], aph ^ 1u, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
@@ -888,7 +940,7 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         tc_fence_after();
         tmem_dealloc(tb, 256);
     }
-    if (tid == 0 && A.partial) {
+    if (tid == 0 && A.partial && !A.bg.live) {
         double tot = 0.0;
         for (int e = 0; e < DSC_EPI_WARPS; ++e) tot += red[e];
         A.partial[blockIdx.x] = tot;
@@ -948,7 +1000,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     __shared__ uint64_t r_full, r_empty, z_full, z_empty, fin_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, never;
-    if (gate_skip(A.gate, A.gate_mode)) return;
+    if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -995,9 +1047,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         uint32_t tcount = 0;
         bool dead = false;
         for (int r = 0;; ++r) {
-            const int k = brick_at(r, G, cta, A.n_bricks);
-            if (k < 0) break;
-            const int brick = A.brick_order[k];
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
             const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
             for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
@@ -1078,9 +1129,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         uint32_t tcount = 0;
         bool stop = false;
         for (int r = 0; !stop; ++r) {
-            const int k = brick_at(r, G, cta, A.n_bricks);
-            if (k < 0) break;
-            const int brick = A.brick_order[k];
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
                 if (!warp_wait(&r_empty, (tcount & 1u) ^ 1u, &abort_flag)) {
                     abort_flag = 1;
@@ -1144,9 +1194,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         uint32_t tcount = 0;
         bool stop = false;
         for (int r = 0; !stop; ++r) {
-            const int k = brick_at(r, G, cta, A.n_bricks);
-            if (k < 0) break;
-            const int brick = A.brick_order[k];
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
                 const uint32_t ph = tcount & 1u;
                 if (!mbar_wait(&r_full, ph, &abort_flag, WAIT_LIMIT) ||
@@ -1182,6 +1231,17 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
 
 // ============================================================== launchers
 
+// WC scatter groups for the next launch: the requested number (4 by default),
+// halved while the kernel's shared memory would not fit; 0 if even 1 does not.
+int wc_effective_groups(const life_index_s* ix) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device) != cudaSuccess) return 0;
+    const TileLayout& L = ix->tile;
+    int wg = ix->wc_groups > 0 ? ix->wc_groups : 4;
+    while (wg >= 1 && wc_smem_bytes(L.np, L.kp, L.max_fb, wg) + 256 > (uint32_t)optin) wg /= 2;
+    return wg;
+}
+
 static TcArgs make_args(life_index_s* ix) {
     TileLayout& L = ix->tile;
     TcArgs A{};
@@ -1211,8 +1271,9 @@ static TcArgs make_args(life_index_s* ix) {
 }
 
 life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
-                   int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s) {
+                   int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s, const BatchGate& bg) {
     TcArgs A = make_args(ix);
+    A.bg = bg;
     if (!A.status) {
         set_error("dsc_tc: no device status word");
         return LIFE_ENOMEM;
@@ -1235,8 +1296,9 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
 }
 
 life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate, int gate_mode,
-                  cudaStream_t s) {
+                  cudaStream_t s, const BatchGate& bg) {
     TcArgs A = make_args(ix);
+    A.bg = bg;
     if (!A.status) {
         set_error("wc_tc: no device status word");
         return LIFE_ENOMEM;
@@ -1247,18 +1309,13 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     A.gate = gate;
     A.gate_mode = gate_mode;
     A.vec4 = (ix->nt % 4 == 0 && (reinterpret_cast<uintptr_t>(r) & 15) == 0) ? 1 : 0;
-    int optin = 0;
-    LIFE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
-    A.wgroups = 4;
-    uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
-    while (smem + 256 > (uint32_t)optin && A.wgroups > 1) {
-        A.wgroups /= 2;
-        smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
-    }
-    if (smem + 256 > (uint32_t)optin) {
-        set_error("wc_tc: %u bytes of shared memory needed, %d available", smem, optin);
+    A.wgroups = wc_effective_groups(ix);
+    if (A.wgroups < 1) {
+        set_error("wc_tc: %u bytes of shared memory needed even with one scatter group",
+                  wc_smem_bytes(A.np, A.kp, A.max_fb, 1));
         return LIFE_ENOTSUP;
     }
+    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
     LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
     wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);
