@@ -119,11 +119,13 @@ def workload_desc(p, nnz):
 class GpuPath:
     """Index + device buffers for one precision/algorithm choice."""
 
-    def __init__(self, life, p, D, b, precision, algo):
+    def __init__(self, life, p, D, b, precision, algo, autotune=False):
         import torch
         self.life = life
         t0 = time.time()
         self.idx = life.upload_problem(p, precision=precision, algo=algo)
+        if autotune:
+            life.life_index_autotune(self.idx)
         torch.cuda.synchronize()
         self.build_s = time.time() - t0
         self.info = self.idx.info()
@@ -249,6 +251,82 @@ def cpu_sample_baseline(p, D32, b, frac_voxels=0.15, reps=3):
     return dict(iter_s=best, frac=frac_nnz, nnz_sample=len(phi), nv_sample=nv_s)
 
 
+def run_batched(life, D, max_iter=500, tol=1e-4):
+    """The batched workload: 16 independent problems of uneven size (Nf log-uniform
+    in 1e4..2e5, cubic grids of edge 32..80, no mask) solved by SBB-NNLS to
+    ‖g~‖/‖g~_0‖ <= tol, as one batched solve (one graph launch) and as 16
+    sequential plain solves, for the FP32 CUDA-core and BF16 tensor-core paths.
+    The BF16 batch's tile layout comes from the autotuner."""
+    import torch
+    import synth
+    t0 = time.time()
+    probs = synth.batched_problems(16)
+    gen_s = time.time() - t0
+    dev = torch.device("cuda")
+    out = {"problems": len(probs), "nnz_raw": int(sum(p.n_raw for p in probs)),
+           "n_fasc": [int(p.n_fasc) for p in probs], "grid_edge": [int(p.grid[0]) for p in probs],
+           "max_iter": max_iter, "tol": tol, "gen_s": gen_s}
+    bs = None
+    s = torch.cuda.current_stream()
+    for name, prec, algo in (("fp32-simt", life.LIFE_FP32, life.LIFE_ALGO_SIMT),
+                             ("bf16-tc", life.LIFE_BF16, life.LIFE_ALGO_TC)):
+        idxs = [life.upload_problem(p, precision=prec, algo=algo) for p in probs]
+        if bs is None:  # b_p = M_p w_true + noise from the FP32 DSC
+            bs = []
+            for p, ix in zip(probs, idxs):
+                b, _ = life.life_dsc(ix, D, torch.from_numpy(p.w_true).to(dev))
+                bs.append(b + torch.from_numpy(p.noise).to(dev))
+        t0 = time.time()
+        batch = life.life_batch_create(idxs, autotune=(algo == life.LIFE_ALGO_TC))
+        torch.cuda.synchronize()
+        create_s = time.time() - t0
+        ws = [torch.ones(p.n_fasc, device=dev) for p in probs]
+        st = life.new_batch_states(len(probs))
+        wsp = life.new_batch_workspace(batch)
+        life.life_batch_solve(batch, D, bs, ws, max_iter, st, wsp, tol=tol)   # builds the graph
+        torch.cuda.synchronize()
+        for w in ws:
+            w.fill_(1.0)
+        st.copy_(life.new_batch_states(len(probs)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        life.life_batch_solve(batch, D, bs, ws, max_iter, st, wsp, tol=tol)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3
+        bst = life.read_batch_states(st, len(probs))
+        # sequential plain solves, each graph built once before timing
+        seq = []
+        for p, ix, b in zip(probs, idxs, bs):
+            w = torch.ones(p.n_fasc, device=dev)
+            st1, ws1 = life.new_sbb_state(), life.new_sbb_workspace(ix)
+            life.life_sbbnnls_solve(ix, D, b, w, 1, st1, ws1, tol=tol)
+            seq.append((ix, b, w, st1, ws1))
+        torch.cuda.synchronize()
+        for ix, b, w, st1, ws1 in seq:
+            w.fill_(1.0)
+            life.life_sbb_state_init(st1)
+        e0.record(s)
+        for ix, b, w, st1, ws1 in seq:
+            life.life_sbbnnls_solve(ix, D, b, w, max_iter, st1, ws1, tol=tol)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_seq = e0.elapsed_time(e1) / 1e3
+        sst = [life.read_sbb_state(x[3]) for x in seq]
+        its_b = [int(x["it"]) for x in bst]
+        its_s = [int(x["it"]) for x in sst]
+        obj_dev = max(abs(a["obj"] - b_["obj"]) / abs(b_["obj"]) for a, b_ in zip(bst, sst))
+        out[name] = {"batched_ms": t_batch * 1e3, "sequential_ms": t_seq * 1e3, "speedup": t_seq / t_batch,
+                     "batched_iter_per_s": sum(its_b) / t_batch, "sequential_iter_per_s": sum(its_s) / t_seq,
+                     "iters": its_b, "iters_sequential": its_s,
+                     "converged": int(sum(x["converged"] for x in bst)),
+                     "max_rel_obj_diff_vs_sequential": obj_dev, "create_s": create_s, "batch": batch.info()}
+        batch.close()
+        for ix in idxs:
+            ix.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -278,7 +356,7 @@ def run_ours(args):
     paths = {"fp32-simt": fp32}
     if args.precision in ("bf16", "both"):
         try:
-            paths["bf16-tc"] = GpuPath(life, p, D, b, life.LIFE_BF16, life.LIFE_ALGO_TC)
+            paths["bf16-tc"] = GpuPath(life, p, D, b, life.LIFE_BF16, life.LIFE_ALGO_TC, autotune=args.autotune)
         except life.LifeError as e:
             paths["bf16-tc"] = None
             if rank == 0:
@@ -321,6 +399,7 @@ def run_ours(args):
     path = best["path"]
     e2e_val, h2d, d2h = e2e_steps(life, path, max(3, args.steps // 2), 2)
     st = life.read_sbb_state(path.st)
+    batched = run_batched(life, D) if args.batched == "on" else None
     if rank != 0:
         if dist:
             dist.barrier()
@@ -362,6 +441,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step(path) * (args.steps) * world,
         "clocks": best["clocks"],
         "final_state": {"it": st["it"], "obj": st["obj"], "alpha": st["alpha"]},
+        "tile_layout": {k: path.info[k] for k in ("brick_edge", "wc_groups", "tuned")},
+        "batched": batched,
         "gen_s": gen_s,
     }
     print(json.dumps(line))
@@ -414,6 +495,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="paper", choices=["paper", "paper_small", "medium", "tiny"])
     ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the autotuner choose the BF16 tile layout of the main workload")
+    ap.add_argument("--batched", default="on", choices=["on", "off"],
+                    help="also time the batched workload (16 problems, batched vs sequential solves)")
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + timed SBB steps inside cudaProfilerStart/Stop, print nothing")
     args = ap.parse_args()

@@ -75,39 +75,23 @@ static life_status upload_vec(DevBuf& dst, const std::vector<T>& src, cudaStream
     return LIFE_OK;
 }
 
-// Launch maps of a batch: the tensor-core grid and DSC partial-sum ranges
-// ([p * grid * epilogue warps, ...) per problem), or the CUDA-core block map
-// (blocks of each problem in proportion to its entries, at least one each, and
-// the problem's DSC partial sums are its blocks' slots).
+// Launch maps of a batch: the per-problem ranges of DSC partial sums.  The
+// tensor-core DSC keeps one per (problem, CTA, epilogue warp), the CUDA-core DSC
+// one per (problem, warp).
 life_status batch_finalize(life_index_s* ix, cudaStream_t s) {
     BatchInfo& bi = ix->batch;
     const int n = bi.n;
     bi.part_off.assign(n + 1, 0);
     if (ix->algo == LIFE_ALGO_TC && ix->tile.built) {
         bi.tc_grid = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ix->num_sms, ix->tile.n_bricks));
+        bi.simt_grid = 0;
         const int epi = 4;  // epilogue warps of the DSC kernel
         for (int p = 0; p <= n; ++p) bi.part_off[p] = p * bi.tc_grid * epi;
     } else {
-        const int64_t total = std::max<int64_t>(bi.nnz_off[n], 1);
-        const int G = ix->num_sms;
-        std::vector<int32_t> count(n), prob, rank;
-        for (int p = 0; p < n; ++p) {
-            const int64_t m = bi.nnz_off[p + 1] - bi.nnz_off[p];
-            count[p] = (int32_t)std::max<int64_t>(1, (m * G + total / 2) / total);
-            bi.part_off[p + 1] = bi.part_off[p] + count[p];
-            for (int r = 0; r < count[p]; ++r) {
-                prob.push_back(p);
-                rank.push_back(r);
-            }
-        }
-        bi.simt_grid = bi.part_off[n];
-        if (bi.simt_grid > RED_SLOTS * 4) {
-            set_error("life_batch_create: %d problems need %d blocks", n, bi.simt_grid);
-            return LIFE_ERANGE;
-        }
-        LIFE_TRY(upload_vec(bi.blk_prob, prob, s));
-        LIFE_TRY(upload_vec(bi.blk_rank, rank, s));
-        LIFE_TRY(upload_vec(bi.blk_count, count, s));
+        bi.tc_grid = 0;
+        bi.simt_grid = ix->num_sms;
+        const int W = simt_total_warps(ix);
+        for (int p = 0; p <= n; ++p) bi.part_off[p] = p * W;
     }
     LIFE_TRY(upload_vec(bi.d_part_off, bi.part_off, s));
     return LIFE_OK;

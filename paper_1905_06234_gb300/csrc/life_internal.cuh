@@ -163,25 +163,20 @@ struct BatchInfo {
     DevBuf brick_prob;                       // TC: int32 [n_bricks] problem of each brick
     int32_t tc_grid = 0;                     // TC: CTAs of a batched SpMV launch
     int32_t simt_grid = 0;                   // SIMT: blocks of a batched SpMV launch
-    DevBuf blk_prob, blk_rank, blk_count;    // SIMT: int32 [grid], [grid], [n]
     std::vector<int32_t> part_off;           // host [n+1] per-problem ranges of DSC partial sums
     DevBuf d_part_off;
 };
 
 // Problem-level gating of a batched launch.  Each work unit (a brick on the TC
-// path, a block on the CUDA-core path) belongs to one problem and runs only while
+// path, a voxel on the CUDA-core path) belongs to one problem and runs only while
 // that problem is live; Eq. 8-only work runs only when the problem's current
 // iteration uses Eq. 8.  live == nullptr means an ordinary single-problem launch.
 struct BatchGate {
     const int32_t* live = nullptr;       // [n] 1 while the problem iterates
     const life_sbb_state* st = nullptr;  // [n] per-problem states
     const int32_t* brick_prob = nullptr; // TC: problem of each brick
-    const int32_t* blk_prob = nullptr;   // SIMT: problem of each block
-    const int32_t* blk_rank = nullptr;   // SIMT: rank of a block among its problem's blocks
-    const int32_t* blk_count = nullptr;  // SIMT: blocks of each problem
-    const int32_t* vox_off = nullptr;    // [n+1]
+    const int32_t* vox_off = nullptr;    // SIMT: [n+1] voxel ranges
     int32_t n = 0;
-    int32_t grid = 0;                    // grid of the batched launch
 };
 
 }  // namespace life
@@ -237,6 +232,8 @@ life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const flo
 life_status wc_simt(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
                     int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
 life_status grad_D_simt(life_index_s* ix, const float* gy, const float* w, float* gD, cudaStream_t s);
+// Warps of one CUDA-core SpMV launch (a batched DSC keeps one partial sum per problem and warp).
+int simt_total_warps(const life_index_s* ix);
 
 // -------------------------------------------------------------- TC SpMVs
 life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,

@@ -455,12 +455,8 @@ life_status sbb_enqueue_batch_step(life_index_s* ix, const float* D, life_sbb_st
     bg.live = W.live;
     bg.st = st;
     bg.brick_prob = bi.brick_prob.as<int32_t>();
-    bg.blk_prob = bi.blk_prob.as<int32_t>();
-    bg.blk_rank = bi.blk_rank.as<int32_t>();
-    bg.blk_count = bi.blk_count.as<int32_t>();
     bg.vox_off = bi.d_vox_off.as<int32_t>();
     bg.n = n;
-    bg.grid = ix->algo == LIFE_ALGO_TC && ix->tile.built ? bi.tc_grid : bi.simt_grid;
     const int32_t* fasc_off = bi.d_fasc_off.as<int32_t>();
     const int32_t* part_off = bi.d_part_off.as<int32_t>();
     const dim3 vgrid(BATCH_VGX, n);

@@ -58,22 +58,9 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
     extern __shared__ float Ds[];
     __shared__ double red[32];
     bool write_y = y != nullptr;
-    int v0, vstep, vend;
-    if (bg.live) {
-        // batched launch: this block serves one problem's voxel range
-        const int p = bg.blk_prob[blockIdx.x];
-        if (!batch_live(bg, p, gate_mode)) return;
-        write_y = write_y && batch_writes_y(bg, p, gate_mode);
-        const int wpb = blockDim.x >> 5;
-        v0 = bg.vox_off[p] + bg.blk_rank[blockIdx.x] * wpb + (threadIdx.x >> 5);
-        vstep = bg.blk_count[p] * wpb;
-        vend = bg.vox_off[p + 1];
-    } else {
+    if (!bg.live) {
         if (gate_skip(gate, gate_mode)) return;
         if (gate && gate_mode == GATE_ACTIVE_Y_EQ8 && gate->eq != 8) write_y = false;
-        v0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        vstep = (gridDim.x * blockDim.x) >> 5;
-        vend = nv;
     }
     constexpr int NTP = NTW * 32;
     if (SMEM_D) {
@@ -81,8 +68,35 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double sq = 0.0;
-    for (int v = v0; v < vend; v += vstep) {
+    // Batched launch: the warps stride over the voxels of all problems and jump
+    // over those of problems that are not live, so the live ones always get the
+    // whole grid; Σ out² goes to a slot per (problem, warp).
+    int p = 0, cur_p = -1;
+    bool live = true, wy = write_y;
+    if (bg.live && partial && lane == 0)
+        for (int q = 0; q < bg.n; ++q) partial[(int64_t)q * warps + wid] = 0.0;
+    for (int v = wid; v < nv; v += warps) {
+        if (bg.live) {
+            if (v >= bg.vox_off[p + 1] || cur_p < 0) {
+                while (v >= bg.vox_off[p + 1]) ++p;
+                live = batch_live(bg, p, gate_mode);
+                wy = write_y && batch_writes_y(bg, p, gate_mode);
+            }
+            if (!live) {
+                // first voxel of this warp's sequence at or after the problem's end
+                const int end = bg.vox_off[p + 1];
+                v += ((end - v + warps - 1) / warps - 1) * warps;
+                continue;
+            }
+            if (p != cur_p) {
+                if (cur_p >= 0 && lane == 0 && partial) partial[(int64_t)cur_p * warps + wid] += sq;
+                sq = 0.0;
+                cur_p = p;
+            }
+        }
         float acc[NTW];
 #pragma unroll
         for (int q = 0; q < NTW; ++q) acc[q] = 0.0f;
@@ -124,13 +138,17 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
                 const int64_t o = t + (int64_t)nt * v;
                 float out = acc[q];
                 if (b) out -= b[o];
-                if (write_y) y[o] = out;
+                if (wy) y[o] = out;
                 sqv = fmaf(out, out, sqv);
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sqv += __shfl_xor_sync(0xffffffffu, sqv, o);
         if (lane == 0) sq += (double)sqv;
+    }
+    if (bg.live) {
+        if (cur_p >= 0 && lane == 0 && partial) partial[(int64_t)cur_p * warps + wid] += sq;
+        return;
     }
     const double tot = block_sum_f64(sq, red);
     if (threadIdx.x == 0 && partial) partial[blockIdx.x] = tot;
@@ -159,27 +177,30 @@ wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__
                int na, int nv, const float* __restrict__ r, float* __restrict__ g, const life_sbb_state* gate,
                int gate_mode, const BatchGate bg) {
     extern __shared__ float Ds[];
-    int v0, vstep, vend;
-    if (bg.live) {
-        const int p = bg.blk_prob[blockIdx.x];
-        if (!batch_live(bg, p, gate_mode)) return;
-        const int wpb = blockDim.x >> 5;
-        v0 = bg.vox_off[p] + bg.blk_rank[blockIdx.x] * wpb + (threadIdx.x >> 5);
-        vstep = bg.blk_count[p] * wpb;
-        vend = bg.vox_off[p + 1];
-    } else {
-        if (gate_skip(gate, gate_mode)) return;
-        v0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        vstep = (gridDim.x * blockDim.x) >> 5;
-        vend = nv;
-    }
+    if (!bg.live && gate_skip(gate, gate_mode)) return;
     constexpr int NTP = NTW * 32;
     if (SMEM_D) {
         stage_D<NTW>(Ds, D, nt, na);
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    for (int v = v0; v < vend; v += vstep) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    int p = 0;
+    bool live = true, first = true;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+        if (bg.live) {
+            // batched launch: skip the voxels of problems that are not live
+            if (first || v >= bg.vox_off[p + 1]) {
+                while (v >= bg.vox_off[p + 1]) ++p;
+                live = batch_live(bg, p, gate_mode);
+                first = false;
+            }
+            if (!live) {
+                const int end = bg.vox_off[p + 1];
+                v += ((end - v + warps - 1) / warps - 1) * warps;
+                continue;
+            }
+        }
         const int beg = vox_ptr[v], end = vox_ptr[v + 1];
         if (beg == end) continue;
         float rr[NTW];
@@ -281,7 +302,7 @@ static life_status launch_dsc(life_index_s* ix, const float* D, const float* w, 
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
     auto kern = dsc_simt_kernel<NTW, SMEM, VT>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = bg.live ? bg.grid : ix->num_sms;
+    const int grid = ix->num_sms;
     kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
                                           ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p), D,
                                           ix->nt, ix->na, ix->nv, w, b, y, partial, gate, gate_mode, bg);
@@ -296,13 +317,15 @@ static life_status launch_wc(life_index_s* ix, const float* D, const float* r, f
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
     auto kern = wc_simt_kernel<NTW, SMEM, VT>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = bg.live ? bg.grid : ix->num_sms;
+    const int grid = ix->num_sms;
     kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
                                           ix->vox.fasc.as<int32_t>(), static_cast<const VT*>(ix->vox.val.p), D,
                                           ix->nt, ix->na, ix->nv, r, g, gate, gate_mode, bg);
     LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
+
+int simt_total_warps(const life_index_s* ix) { return ix->num_sms * (SIMT_THREADS / 32); }
 
 life_status dsc_simt(life_index_s* ix, const float* D, const float* w, const float* b, float* y, double* partial,
                      int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s, const BatchGate& bg) {
