@@ -222,7 +222,8 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
                             &idx->tile.tile_vox, &idx->tile.sub_ptr, &idx->tile.brick_tile_ptr,
                             &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
                             &idx->tile.va, &idx->tile.soff, &idx->tile.fl, &idx->tile.val, &idx->tile.wkey,
-                            &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->red};
+                            &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->tile.wb_src,
+                            &idx->tile.wb_ptr, &idx->tile.wb, &idx->red};
     int64_t tot = 0;
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;

@@ -149,6 +149,13 @@ struct TileLayout {
     DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom sub)
     DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
     DevBuf val;              // bf16 [n_nnz]
+    // DSC brick weight tables: brick b's weights w[brick_fasc[...]] are gathered,
+    // before each DSC launch, into wb[wb_ptr[b] ..) (16-byte aligned, padded to a
+    // multiple of 4 floats) so a CTA loads a brick's table with one bulk copy
+    int64_t wb_total = 0;
+    DevBuf wb_src;           // int32 [wb_total]: global fascicle of each slot (0 for padding)
+    DevBuf wb_ptr;           // int32 [n_bricks + 1], multiples of 4
+    DevBuf wb;               // float [wb_total]: gathered weights (rewritten by every DSC call)
 };
 
 // A block-diagonal index that concatenates several problems (batched solve):

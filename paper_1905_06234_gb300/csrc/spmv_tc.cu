@@ -91,6 +91,22 @@ __global__ void brick_fasc_kernel(const uint64_t* __restrict__ key2, int64_t m, 
     }
 }
 
+// wb_src[wb_ptr[b] + i] = brick_fasc[brick_fasc_ptr[b] + i], padding slots 0 (one block per brick).
+__global__ void wb_src_kernel(const int32_t* __restrict__ bptr, const int32_t* __restrict__ bfasc,
+                              const int32_t* __restrict__ wptr, int32_t nb, int32_t* __restrict__ wsrc) {
+    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int32_t f0 = bptr[b], n = bptr[b + 1] - f0, o = wptr[b], np = wptr[b + 1] - o;
+        for (int32_t i = threadIdx.x; i < np; i += blockDim.x) wsrc[o + i] = i < n ? bfasc[f0 + i] : 0;
+    }
+}
+
+// wb[j] = w[wb_src[j]]: the DSC's brick weight tables for this call's w.
+__global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
+                                 float* __restrict__ wb) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        wb[j] = __ldg(w + wsrc[j]);
+}
+
 // Brick-local fascicle number of each entry, scattered back to tile order.
 // uidx is the exclusive scan of the head flags, so an entry that repeats its
 // predecessor's (brick, fascicle) belongs to unique index uidx - 1.
@@ -341,6 +357,22 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     L.n_tiles = H.n_tiles;
     L.n_bricks = H.n_bricks;
     L.n_nnz = m;
+    {
+        // padded, 16-byte aligned per-brick weight slots for the DSC's bulk table loads
+        std::vector<int32_t> wptr(H.n_bricks + 1, 0);
+        for (int64_t b = 0; b < H.n_bricks; ++b) wptr[b + 1] = wptr[b] + (hbptr[b + 1] - hbptr[b] + 3) / 4 * 4;
+        L.wb_total = wptr[H.n_bricks];
+        LIFE_TRY(upload(L.wb_ptr, wptr, s));
+        LIFE_TRY(L.wb_src.alloc(sizeof(int32_t) * std::max<int64_t>(L.wb_total, 4)));
+        LIFE_TRY(L.wb.alloc(sizeof(float) * std::max<int64_t>(L.wb_total, 4)));
+        if (H.n_bricks > 0) {
+            wb_src_kernel<<<(unsigned)std::min<int64_t>(H.n_bricks, 65535), 128, 0, s>>>(
+                L.brick_fasc_ptr.as<int32_t>(), L.brick_fasc.as<int32_t>(), L.wb_ptr.as<int32_t>(),
+                (int32_t)H.n_bricks, L.wb_src.as<int32_t>());
+            LIFE_CHECK_LAUNCH();
+        }
+        LIFE_CUDA_TRY(cudaStreamSynchronize(s));  // wptr is a host temporary
+    }
     if (!ix->batch.vox_group.empty()) {
         // problem of each brick (every voxel of a brick belongs to one problem; row 0
         // of a brick's first tile is always a voxel)
@@ -472,6 +504,8 @@ struct TcArgs {
     const float* b;      // DSC residual or NULL
     float* out;          // DSC: y (or NULL);   WC: g (zeroed by the caller)
     double* partial;     // DSC: per-CTA FP64 Σ out²
+    const float* wb;     // DSC: gathered brick weight tables
+    const int32_t* wb_ptr;
     const life_sbb_state* gate;
     int gate_mode;
     uint32_t* status;
@@ -553,27 +587,6 @@ __device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int 
     return true;
 }
 
-// dst[i] = src[idx[i]] for i < n, with eight independent loads in flight per thread.
-__device__ __forceinline__ void gather_table(float* dst, const float* __restrict__ src,
-                                             const int32_t* __restrict__ idx, int n, int tid, int nthr) {
-    for (int b0 = 0; b0 < n; b0 += 8 * nthr) {
-        int id[8];
-        float v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int i = b0 + e * nthr + tid;
-            id[e] = i < n ? __ldg(idx + i) : -1;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = id[e] >= 0 ? __ldg(src + id[e]) : 0.0f;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int i = b0 + e * nthr + tid;
-            if (i < n) dst[i] = v[e];
-        }
-    }
-}
-
 // dst[idx[i]] += tab[i] for every non-zero tab[i], i < n (one atomic per fascicle).
 __device__ __forceinline__ void flush_table(float* dst, const float* tab, const int32_t* __restrict__ idx, int n,
                                             int tid, int nthr) {
@@ -604,10 +617,14 @@ constexpr int DSTAGE = 2;                                 // S-chunk ring depth
 constexpr uint32_t DS_BYTES = TILE_V * DKC * 2;           // one S chunk: 128 rows x 128 atoms, bf16
 constexpr uint32_t DS_SBO = (DKC / 8) * 128;              // 8-row group stride of an S chunk
 
+// All-zero source of the bulk copies that clear an S stage (zero-initialised
+// device memory, read through L2).
+static __device__ __align__(128) uint4 g_zero_chunk[DS_BYTES / 16];
+
 __host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb) {
     uint32_t d = (uint32_t)np * kp * 2;
     d = (d + 1023) / 1024 * 1024;
-    return d + DSTAGE * DS_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+    return d + DSTAGE * DS_BYTES + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) + 1024;
 }
 
 __device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s) {
@@ -684,9 +701,11 @@ __device__ __forceinline__ void dsc_flush_sq(const TcArgs& A, double& sq, int p,
 
 __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar;
+    __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
+        tab_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, never;
+    __shared__ int chunk_next[DSTAGE];  // next dynamically handed-out 256-entry block of the stage's chunk
     __shared__ double red[DSC_EPI_WARPS];
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
     const bool write_y = A.out != nullptr && (A.bg.live || !(A.gate && A.gate_mode == GATE_ACTIVE_Y_EQ8 &&
@@ -710,7 +729,10 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         for (int s = 0; s < DSTAGE; ++s) {
             mbar_init(&full_bar[s], DSC_PROD_WARPS);
             mbar_init(&empty_bar[s], 1);
+            mbar_init(&zero_bar[s], 1);
+            chunk_next[s] = DSC_PROD_WARPS;
         }
+        mbar_init(&tab_bar, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], DSC_EPI_WARPS);
@@ -745,25 +767,34 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
             bool have = base < end;
             EntrySlot cur{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
             if (have) load_slot(A.soff, A, base, cur);
-            bool new_brick = true;
-            uint32_t cc = 0;
+            bool new_brick = true, dead = false;
+            uint32_t cc = 0, tab_ph = 0, tab_n = 0;
             for (;;) {
                 if (new_brick) {
-                    const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
-                    named_bar_sync(1, DSC_PROD_THREADS);
-                    gather_table(wl, A.x, A.brick_fasc + fb0, nfb, tid, DSC_PROD_THREADS);
-                    named_bar_sync(1, DSC_PROD_THREADS);
+                    // every producer is done with the previous brick's weights (and
+                    // all take the same abort decision) before the table is replaced
+                    if (named_bar_or(1, DSC_PROD_THREADS, dead || abort_flag != 0)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    if (tid == 0) {  // one bulk copy of the brick's gathered weights
+                        const int o = A.wb_ptr[brick], nb4 = A.wb_ptr[brick + 1] - o;
+                        mbar_arrive_expect_tx(&tab_bar, 4u * (uint32_t)nb4);
+                        if (nb4 > 0) bulk_copy_g2s(wl, A.wb + o, 4u * (uint32_t)nb4, &tab_bar);
+                    }
+                    if (!warp_wait(&tab_bar, tab_ph, &abort_flag)) {
+                        abort_flag = 1;
+                        dead = true;
+                    }
+                    tab_ph ^= 1u;
+                    ++tab_n;
                 }
                 const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
                 unsigned char* S = Ss + st * DS_BYTES;
-                const bool fail = !warp_wait(&empty_bar[st], ph ^ 1u, &abort_flag);
-                if (!fail) {
-                    uint4* z = reinterpret_cast<uint4*>(S);
-                    for (int q = tid; q < (int)(DS_BYTES / 16); q += DSC_PROD_THREADS) z[q] = make_uint4(0, 0, 0, 0);
-                }
-                if (named_bar_or(1, DSC_PROD_THREADS, fail || abort_flag != 0)) {
+                // the stage is free and cleared once the MMA thread's bulk zero copy lands
+                if (!dead && !warp_wait(&zero_bar[st], ph, &abort_flag)) {
                     abort_flag = 1;
-                    break;
+                    dead = true;
                 }
                 int nr = r, nbrick = brick, nt = t, nc = c;
                 bool nnew = false;
@@ -777,11 +808,18 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 const bool nhave = nvalid && nbase < nend;
                 EntrySlot nxt{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
                 bool pf = false;
-                // every lane of a warp runs the same number of slot steps (the
-                // warp's first lane decides), so dsc_slot can shuffle
-                while (__shfl_sync(0xffffffffu, base, 0) < end) {
-                    const int b2 = base + DSC_PROD_THREADS * SLOT;
-                    const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;  // warp-uniform
+                // The chunk is cut into 256-entry blocks (one slot per lane): warp w
+                // takes block w, then blocks handed out by the stage's counter, so
+                // the warps finish a chunk together.  Every lane of a warp runs the
+                // same number of slot steps, so dsc_slot can shuffle.
+                const int bb = beg & ~7;
+                int blk = warp;
+                while (!dead && bb + blk * (32 * SLOT) < end) {
+                    int nb = 0;
+                    if (lane == 0) nb = atomicAdd(&chunk_next[st], 1);
+                    nb = __shfl_sync(0xffffffffu, nb, 0);
+                    const int b2 = bb + nb * (32 * SLOT) + lane * SLOT;
+                    const bool more = bb + nb * (32 * SLOT) < end;  // warp-uniform
                     if (more) {
                         if (b2 < end) load_slot(A.soff, A, b2, nxt);
                         else nxt = EntrySlot{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
@@ -793,11 +831,12 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                     if (!more) break;
                     cur = nxt;
                     base = b2;
+                    blk = nb;
                 }
                 if (!pf && nhave) load_slot(A.soff, A, nbase, nxt);
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&full_bar[st]);
+                if (lane == 0 && !dead) mbar_arrive(&full_bar[st]);
                 ++cc;
                 if (!nvalid) break;
                 r = nr;
@@ -811,6 +850,8 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                 have = nhave;
                 cur = nxt;  // an empty slot when this lane has none in the next chunk
             }
+            // no bulk table copy may still be writing shared memory when the CTA exits
+            if (tid == 0 && tab_n > 0) mbar_wait(&tab_bar, (tab_n - 1) & 1u, &never, WAIT_LIMIT);
         }
     } else if (warp < DSC_MMA_WARP) {
         // ---------------- epilogue: TMEM -> y (− b), Σ y² (FP32 per row and tile, FP64 across)
@@ -903,7 +944,12 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)A.np);
         const uint32_t sS = smem_u32(Ss), sD = smem_u32(Ds);
         uint32_t cc = 0, tcount = 0;
+        uint32_t zlast = 0;  // bit z: parity of the last zero-copy phase issued on stage z
         bool stop = false;
+        for (int z = 0; z < DSTAGE; ++z) {  // clear both stages for their first use
+            mbar_arrive_expect_tx(&zero_bar[z], DS_BYTES);
+            bulk_copy_g2s(Ss + z * DS_BYTES, g_zero_chunk, DS_BYTES, &zero_bar[z]);
+        }
         for (int r = 0; !stop; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
@@ -923,6 +969,12 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
                         mma_bf16(d, ad, bd, idesc, (c | kk) != 0 ? 1u : 0u);
                     }
                     mma_commit(&empty_bar[st]);
+                    // once these MMAs have read the stage, clear it for its next use
+                    if (!mbar_wait(&empty_bar[st], ph, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
+                    chunk_next[st] = DSC_PROD_WARPS;  // published by the arrive below
+                    mbar_arrive_expect_tx(&zero_bar[st], DS_BYTES);
+                    bulk_copy_g2s(Ss + st * DS_BYTES, g_zero_chunk, DS_BYTES, &zero_bar[st]);
+                    zlast ^= 1u << st;
                     ++cc;
                 }
                 if (stop) break;
@@ -932,6 +984,8 @@ __global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
         }
         mma_commit(&fin_bar);
         mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT);
+        // no bulk copy may still be writing shared memory when the CTA exits
+        for (int z = 0; z < DSTAGE; ++z) mbar_wait(&zero_bar[z], (zlast >> z) & 1u, &never, WAIT_LIMIT);
     }
     if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     tc_fence_before();
@@ -1259,6 +1313,8 @@ static TcArgs make_args(life_index_s* ix) {
     A.wseg_ptr = L.wseg_ptr.as<int32_t>();
     A.fl = L.fl.as<uint16_t>();
     A.val = L.val.as<__nv_bfloat16>();
+    A.wb = L.wb.as<float>();
+    A.wb_ptr = L.wb_ptr.as<int32_t>();
     A.nt = ix->nt;
     A.na = ix->na;
     A.np = L.np;
@@ -1287,6 +1343,11 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
     A.gate_mode = gate_mode;
     A.vec4 = (ix->nt % 4 == 0 && ((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) ? 1 : 0;
     const uint32_t smem = dsc_smem_bytes(A.np, A.kp, A.max_fb);
+    if (ix->tile.wb_total > 0) {
+        wb_gather_kernel<<<ix->num_sms * 8, 256, 0, s>>>(ix->tile.wb_src.as<int32_t>(), ix->tile.wb_total, w,
+                                                        ix->tile.wb.as<float>());
+        LIFE_CHECK_LAUNCH();
+    }
     LIFE_CUDA_TRY(cudaFuncSetAttribute(dsc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
     dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
