@@ -193,27 +193,36 @@ struct HostTiles {
     int64_t n_tiles = 0, n_bricks = 0;
 };
 
-// Groups voxels into bricks (spatial B^3 cubes when coordinates are known,
-// else runs of B^3 consecutive voxel ids) and each brick into 128-voxel tiles.
-// For the combined index of a batch, bricks never mix problems: the problem is
-// the leading part of the brick key, and voxel-id runs restart at each problem.
-static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, int B, const BatchInfo& bi, HostTiles& H) {
+// Groups voxels into bricks (spatial bx x by x bz boxes when coordinates are
+// known, else runs of bx*by*bz consecutive voxel ids) and each brick into
+// 128-voxel tiles.  shape[g] is the brick shape of group g (one group, or one per
+// problem of a batch).  For the combined index of a batch, bricks never mix
+// problems: the problem is the leading part of the brick key, and voxel-id runs
+// restart at each problem.
+struct BrickShape {
+    int x, y, z;
+    int64_t volume() const { return (int64_t)x * y * z; }
+};
+
+static void assign_tiles(int32_t nv, const std::vector<int32_t>& ijk, const std::vector<BrickShape>& shape,
+                         const BatchInfo& bi, HostTiles& H) {
     std::vector<int64_t> bkey(nv);
     const bool grouped = !bi.vox_group.empty();
-    if (!ijk.empty()) {
-        int32_t mx[3] = {0, 0, 0};
+    int32_t mx[3] = {0, 0, 0};
+    if (!ijk.empty())
         for (int32_t v = 0; v < nv; ++v)
             for (int d = 0; d < 3; ++d) mx[d] = std::max(mx[d], ijk[3 * v + d]);
-        const int64_t nbx = mx[0] / B + 1, nby = mx[1] / B + 1;
-        for (int32_t v = 0; v < nv; ++v)
-            bkey[v] = ((int64_t)(ijk[3 * v + 2] / B) * nby + ijk[3 * v + 1] / B) * nbx + ijk[3 * v] / B;
-    } else {
-        const int64_t bs = (int64_t)B * B * B;
-        for (int32_t v = 0; v < nv; ++v)
-            bkey[v] = (grouped ? v - bi.vox_off[bi.vox_group[v]] : v) / bs;
+    for (int32_t v = 0; v < nv; ++v) {
+        const int g = grouped ? bi.vox_group[v] : 0;
+        const BrickShape& sh = shape[g];
+        if (!ijk.empty()) {
+            const int64_t nbx = mx[0] / sh.x + 1, nby = mx[1] / sh.y + 1;
+            bkey[v] = ((int64_t)(ijk[3 * v + 2] / sh.z) * nby + ijk[3 * v + 1] / sh.y) * nbx + ijk[3 * v] / sh.x;
+        } else {
+            bkey[v] = (grouped ? v - bi.vox_off[g] : v) / sh.volume();
+        }
+        if (grouped) bkey[v] |= (int64_t)g << 40;
     }
-    if (grouped)
-        for (int32_t v = 0; v < nv; ++v) bkey[v] |= (int64_t)bi.vox_group[v] << 40;
     std::vector<int32_t> order(nv);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bkey[x] < bkey[y]; });
@@ -292,10 +301,15 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     LIFE_TRY(uidx.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
     int32_t n_unique = 0;
     bool ok = false;
+    // Every group starts from B0^3 bricks; a group whose largest brick fascicle
+    // table overflows halves its brick's largest dimension and the layout is
+    // rebuilt, until all groups fit (other groups keep their bricks).
     const int B0 = std::max(2, ix->brick_dim);
-    for (int B : {B0, B0 * 3 / 4, B0 / 2, B0 / 4}) {
-        if (B < 1) continue;
-        assign_tiles(ix->nv, ijk, B, ix->batch, H);
+    const bool grouped = !ix->batch.vox_group.empty();
+    const int ngroups = grouped ? ix->batch.n : 1;
+    std::vector<BrickShape> shape(ngroups, BrickShape{B0, B0, B0});
+    for (int attempt = 0; attempt < 32 && !ok; ++attempt) {
+        assign_tiles(ix->nv, ijk, shape, ix->batch, H);
         LIFE_TRY(upload(d_vox_tile, H.vox_tile, s));
         LIFE_TRY(upload(d_vox_row, H.vox_row, s));
         LIFE_TRY(upload(d_tile_brick, H.tile_brick, s));
@@ -339,15 +353,34 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         LIFE_CUDA_TRY(cudaMemcpyAsync(hbptr.data(), L.brick_fasc_ptr.p, sizeof(int32_t) * hbptr.size(),
                                       cudaMemcpyDeviceToHost, s));
         LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int32_t> gmax(ngroups, 0);
         int32_t mx = 0;
-        for (int64_t b = 0; b < H.n_bricks; ++b) mx = std::max(mx, hbptr[b + 1] - hbptr[b]);
-        L.max_fb = mx;
-        L.brick_edge = ijk.empty() ? 0 : B;
-        L.brick_b = B;
-        if (mx <= MAX_BRICK_FASC) {
-            ok = true;
-            break;
+        for (int64_t b = 0; b < H.n_bricks; ++b) {
+            const int32_t nfb = hbptr[b + 1] - hbptr[b];
+            const int g = grouped ? ix->batch.vox_group[H.tile_vox[(size_t)H.brick_tile_ptr[b] * TILE_V]] : 0;
+            gmax[g] = std::max(gmax[g], nfb);
+            mx = std::max(mx, nfb);
         }
+        L.max_fb = mx;
+        ok = true;
+        bool shrunk = false;
+        for (int g = 0; g < ngroups; ++g) {
+            if (gmax[g] <= MAX_BRICK_FASC) continue;
+            ok = false;
+            BrickShape& sh = shape[g];
+            int* d = sh.x >= sh.y && sh.x >= sh.z ? &sh.x : (sh.y >= sh.z ? &sh.y : &sh.z);
+            if (*d > 1) {
+                *d = (*d + 1) / 2;
+                shrunk = true;
+            }
+        }
+        if (!ok && !shrunk) break;
+    }
+    {
+        const BrickShape& s0 = shape[0];
+        const bool cubic = s0.x == s0.y && s0.y == s0.z;
+        L.brick_edge = ijk.empty() ? 0 : (cubic ? s0.x : std::max(s0.x, std::max(s0.y, s0.z)));
+        L.brick_b = B0;
     }
     if (!ok) {
         set_error("tensor-core layout: a brick touches %d fascicles (limit %d) even at the smallest brick",

@@ -153,9 +153,17 @@ def test_batch_solve_matches_sequential_fp32(life, bt):
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_batch_step_teacher_forced(life, bt, precision):
     """Each batched iteration against a single-problem iteration started from the
-    batch's own iterate and state, so drift cannot accumulate.  With BF16 storage
-    the v' = M g~ product rounds S = Σ val·g~ to BF16, so a last-bit difference in
-    g (atomic order) can flip single roundings: hence the looser bound there."""
+    batch's own iterate and state, so drift cannot accumulate.
+
+    FP32 (CUDA cores): per-voxel sums in the same order on both sides, so only
+    WC's atomic order differs.  BF16 (tensor cores): a run sum Σ val·w of one
+    (atom, row) is split at 8-entry slot boundaries, which sit at different
+    offsets of the combined stream than of the problem's own stream, so the FP32
+    association differs and, now and then, one BF16 rounding of an S cell lands on
+    the other neighbour (a 2^-8 relative change of one term of one voxel).  The
+    same happens in v' = M g~ when g differs in its last bits (atomic order).
+    Both results satisfy the BF16 error bounds; the bounds below allow a few such
+    flips."""
     idxs, batch = make(life, bt, precision)
     bf = precision == "bf16"
     n = len(bt.probs)
@@ -178,11 +186,12 @@ def test_batch_step_teacher_forced(life, bt, precision):
             ref = life.read_sbb_state(st_in[k])
             assert got[k]["it"] == ref["it"] == it + 1 and got[k]["eq"] == ref["eq"]
             for key in ("obj", "gg"):
-                assert abs(got[k][key] - ref[key]) <= 1e-6 * abs(ref[key]), (it, k, key, got[k][key], ref[key])
-            for key in ("vv", "uu", "alpha"):
-                tol = 3e-4 if bf else 1e-5
+                tol = 2e-4 if bf else 1e-6
                 assert abs(got[k][key] - ref[key]) <= tol * abs(ref[key]), (it, k, key, got[k][key], ref[key])
-            assert rel(ws[k].cpu().numpy(), w_in[k].cpu().numpy()) <= (1e-3 if bf else 1e-5)
+            for key in ("vv", "uu", "alpha"):
+                tol = 5e-3 if bf else 1e-5
+                assert abs(got[k][key] - ref[key]) <= tol * abs(ref[key]), (it, k, key, got[k][key], ref[key])
+            assert rel(ws[k].cpu().numpy(), w_in[k].cpu().numpy()) <= (5e-3 if bf else 1e-5)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
