@@ -30,23 +30,21 @@ UNIT = "iter/s"
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
-# DRAM bytes (read + write) of one launch of each tensor-core kernel, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the paper-density
-# workload at one third of the size (64x64x48 grid, Nf = 150k, nnz = 23,816,750):
-# the DSC launch with the fused residual and the WC launch of an SBB iteration.
-# A full-size launch is scaled by the entries processed (the dense vectors grow
-# with the voxels, in the same proportion).  The figures hold only for the kernel
-# source that was captured; after any change to it the bench reports null.
+# DRAM bytes (read + write) of one launch of each tensor-core kernel on the
+# paper-scale workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, a one-pass metric set): the DSC launch with the fused
+# residual and the WC launch of an SBB iteration.  The figures hold only for the
+# kernel source that was captured; after any change to it the bench reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "00b26a789f1397c3e7d91bf4c20b9d7bb57f10534f1f925f20d71aaa3b758782",
-    "nnz": 23816750,
-    "bytes": {"dsc": 194816768 + 22027776, "wc": 194358272 + 3185408},
+    "sha256": "a81535d3df72c9e79b0546835e1bd7f92d9eff297ce3deaec85164986e7cd70b",
+    "nnz": 79521683,
+    "bytes": {"dsc": 649105152 + 114766848, "wc": 656038656 + 5112576},
 }
 
 
 def kernel_traffic(path_name, kind, nnz):
-    """Measured DRAM bytes of one launch scaled to `nnz` entries, or None."""
+    """Measured DRAM bytes of one launch (scaled to `nnz` entries if the workload differs), or None."""
     import hashlib
     if not path_name.startswith("bf16-tc"):
         return None
@@ -457,7 +455,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
                      "traffic": kernel_traffic(best_name, dom, path.info["nnz"]),
-                     "traffic_note": "ncu DRAM bytes of one launch at one third size, scaled by entries"},
+                     "traffic_note": "ncu DRAM bytes of one launch of this kernel on this workload"},
         "dsc_wc": {"gbs": dsc_wc_gbs, "frac_of_peak": dsc_wc_gbs / peak, "dsc_ms": kern["dsc_s"] * 1e3,
                    "wc_ms": kern["wc_s"] * 1e3},
         "paths": {k: {"iter_per_s": args.steps / v["dt"], "dsc_ms": v["kern"]["dsc_s"] * 1e3,
