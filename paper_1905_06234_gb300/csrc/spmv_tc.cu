@@ -101,10 +101,21 @@ __global__ void wb_src_kernel(const int32_t* __restrict__ bptr, const int32_t* _
 }
 
 // wb[j] = w[wb_src[j]]: the DSC's brick weight tables for this call's w.
+// (n is a multiple of 4 and both arrays are 16-byte aligned: each thread moves 4
+// slots per step with one 16-byte load of indices, four independent gathers and
+// one 16-byte store.)
 __global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
                                  float* __restrict__ wb) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        wb[j] = __ldg(w + wsrc[j]);
+    const int64_t n4 = n >> 2;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
+        const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
+        float4 v;
+        v.x = __ldg(w + id.x);
+        v.y = __ldg(w + id.y);
+        v.z = __ldg(w + id.z);
+        v.w = __ldg(w + id.w);
+        reinterpret_cast<float4*>(wb)[j] = v;
+    }
 }
 
 // Brick-local fascicle number of each entry, scattered back to tile order.
@@ -640,7 +651,7 @@ __device__ __forceinline__ void flush_table(float* dst, const float* tab, const 
 
 // ---------------------------------------------------------------------- DSC
 
-constexpr int DSC_PROD_WARPS = 15;   // 20 warps in all: 5 per SM sub-partition fit 96 registers
+constexpr int DSC_PROD_WARPS = 19;   // 24 warps in all: 6 per SM sub-partition fit 80 registers
 constexpr int DSC_EPI_WARPS = 4;
 constexpr int DSC_MMA_WARP = DSC_PROD_WARPS + DSC_EPI_WARPS;
 constexpr int DSC_THREADS = (DSC_MMA_WARP + 1) * 32;
@@ -732,7 +743,7 @@ __device__ __forceinline__ void dsc_flush_sq(const TcArgs& A, double& sq, int p,
     sq = 0.0;
 }
 
-__global__ void __maxnreg__(96) dsc_tc_kernel(TcArgs A) {
+__global__ void __maxnreg__(80) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
         tab_bar;
