@@ -349,6 +349,16 @@ LIFE_API life_status life_batch_solve(life_batch batch, const float* D, const fl
  */
 LIFE_API life_status life_index_autotune(life_index idx, void* stream);
 
+/*
+ * Self-test of failure detection: launches a kernel whose single wait can never
+ * complete; it gives up after limit_ns nanoseconds (1 .. 2e9) of wall-clock time
+ * and records a timeout in the device status word, exactly as a stalled pipeline
+ * in the persistent kernels would.  Nothing faults or traps.  A following
+ * life_check_device_status() returns LIFE_ETIMEOUT (and clears the word); the
+ * context stays usable.  Asynchronous on `stream`.
+ */
+LIFE_API life_status life_selftest_bounded_wait(int64_t limit_ns, void* stream);
+
 /* Checks the device status word every bounded wait in this library writes to;
  * returns LIFE_ETIMEOUT (and clears the word) if one gave up.  Synchronizes. */
 LIFE_API life_status life_check_device_status(void* stream);

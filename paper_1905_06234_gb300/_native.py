@@ -28,7 +28,8 @@ EXPORTS = [
     "life_dsc_grad_D", "life_dsc_grad_D_noalloc", "life_dictionary", "life_dot_f32", "life_sbb_workspace_bytes", "life_sbb_state_init",
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_batch_create", "life_batch_free", "life_batch_get_info",
     "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
-    "life_index_autotune", "life_check_device_status", "life_last_error", "life_version",
+    "life_index_autotune", "life_selftest_bounded_wait", "life_check_device_status", "life_last_error",
+    "life_version",
 ]
 
 
@@ -112,6 +113,7 @@ def load(build_if_missing: bool = False):
     L.life_batch_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.life_batch_solve.argtypes = [P, P, P, P, i64, dbl, i32, P, P, P]
     L.life_index_autotune.argtypes = [P, P]
+    L.life_selftest_bounded_wait.argtypes = [i64, P]
     L.life_check_device_status.argtypes = [P]
     L.life_last_error.restype = ctypes.c_char_p
     L.life_version.restype = ctypes.c_char_p
@@ -483,3 +485,8 @@ def life_batch_solve(batch: LifeBatch, D, bs, ws, max_iter, st, workspace, tol=0
     wp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ws])
     _check(load().life_batch_solve(batch.handle, _ptr(D), bp, wp, int(max_iter), float(tol),
                                    1 if eq7_on_even else 0, _ptr(st), _aligned(workspace), _stream()))
+
+
+def life_selftest_bounded_wait(limit_ns: int):
+    """Runs a wait that cannot complete, bounded to limit_ns (see include/life.h)."""
+    _check(load().life_selftest_bounded_wait(int(limit_ns), _stream()))

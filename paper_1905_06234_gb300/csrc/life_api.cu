@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "life_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace life {
 
@@ -395,6 +396,44 @@ extern "C" life_status life_sbbnnls_solve(life_index idx, const float* D, const 
         }
     }
     return LIFE_OK;
+}
+
+namespace life {
+
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// arrives at, gives up after limit_ns and records DEV_TIMEOUT, as a stalled
+// tensor-core pipeline would.  Nothing faults or traps; the context stays usable.
+__global__ void bounded_wait_probe_kernel(uint32_t* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int never;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        never = 0;
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !ptx::mbar_wait(&bar, 0, &never, limit_ns)) atomicOr(status, DEV_TIMEOUT);
+}
+
+life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s) {
+    uint32_t* status = dev_status_word();
+    if (!status) {
+        set_error("bounded wait probe: no device status word");
+        return LIFE_ENOMEM;
+    }
+    bounded_wait_probe_kernel<<<1, 32, 0, s>>>(status, (uint64_t)limit_ns);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+}  // namespace life
+
+extern "C" life_status life_selftest_bounded_wait(int64_t limit_ns, void* stream) {
+    if (limit_ns < 1 || limit_ns > 2000000000ll) {
+        set_error("life_selftest_bounded_wait: limit_ns must be in [1, 2e9]");
+        return LIFE_EINVAL;
+    }
+    return bounded_wait_probe(limit_ns, (cudaStream_t)stream);
 }
 
 extern "C" life_status life_check_device_status(void* stream) {

@@ -262,6 +262,7 @@ life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int
 // (rebuilds the tile layout); a no-op on the CUDA-core path.
 life_status autotune_tc(life_index_s* ix, cudaStream_t s);
 int wc_effective_groups(const life_index_s* ix);
+life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s);
 // Per-problem launch maps of a batch's combined index (after its layouts are built).
 life_status batch_finalize(life_index_s* ix, cudaStream_t s);
 

@@ -333,3 +333,25 @@ def test_sbb_converged_state_is_noop(life, tiny):
     s = life.read_sbb_state(st)
     assert s["converged"] == 1 and s["it"] == 0
     assert float(w.min()) == 1.0 and float(w.max()) == 1.0
+
+
+# ------------------------------------------------------- failure detection
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(life, tiny):
+    """A wait that can never complete gives up after its limit, the host reads
+    LIFE_ETIMEOUT from the status word (which is then cleared), and the next
+    SpMV on the same context is still correct.  Nothing faults."""
+    life.life_check_device_status()                       # start clean
+    life.life_selftest_bounded_wait(50_000_000)           # 50 ms
+    with pytest.raises(life.LifeError) as ei:
+        life.life_check_device_status()
+    assert ei.value.status == life._native.LIFE_ETIMEOUT
+    life.life_check_device_status()                       # cleared
+    p = tiny.p
+    idx = life.upload_problem(p)
+    w = np.random.default_rng(2).random(p.n_fasc).astype(np.float32)
+    y, _ = life.life_dsc(idx, dev(tiny.D32), dev(w))
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), oracle.dsc(tiny.phi, tiny.D32, w, p.n_theta, p.n_voxels)) <= TOL_FP32
+    with pytest.raises(life.LifeError):
+        life.life_selftest_bounded_wait(0)                # argument check
