@@ -257,9 +257,13 @@ LIFE_API life_status life_sbbnnls_step(life_index idx, const float* D, const flo
                               void* stream);
 
 /*
- * Up to max_iter iterations of life_sbbnnls_step, replayed from a CUDA graph the
- * index caches for these pointers.  With tol > 0 the host polls the state every
- * 64 iterations (a stream synchronization) and stops early once converged.
+ * Up to max_iter iterations of life_sbbnnls_step as ONE CUDA graph launch: a
+ * conditional WHILE node whose body is one iteration and a kernel that decides on
+ * the device whether to iterate again (until the state has converged, i.e.
+ * <g~,g~> = 0 or ‖g~‖ <= tol·‖g~_0‖, or max_iter iterations ran in this call).
+ * Asynchronous; the graph is cached in the index for the same pointers, tol and
+ * rule (max_iter is read from the workspace at run time).  The first call for a
+ * configuration must not be inside a stream capture.
  */
 LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const float* b, float* w,
                                int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
@@ -335,8 +339,9 @@ LIFE_API life_status life_batch_workspace_bytes(life_batch batch, size_t* bytes)
  *             [Nf_p] (updated in place)
  *  st         device array of n states (life_sbb_state_init each, or continue)
  *  workspace  device, life_batch_workspace_bytes() bytes, 256-byte aligned
- * Asynchronous; the graph is cached for the same D, st, workspace, tol, rule and
- * max_iter.  The first call for a configuration must not be inside a stream capture.
+ * Asynchronous; the graph is cached for the same D, st, workspace, tol and rule
+ * (max_iter is read from the workspace at run time).  The first call for a
+ * configuration must not be inside a stream capture.
  */
 LIFE_API life_status life_batch_solve(life_batch batch, const float* D, const float* const* b, float* const* w,
                                       int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,

@@ -26,7 +26,6 @@ struct life_batch_s {
     const void* graph_key[3] = {nullptr, nullptr, nullptr};
     double graph_tol = -1.0;
     int graph_eq7 = -1;
-    int64_t graph_max_iter = -1;
     ~life_batch_s() {
         if (graph) cudaGraphExecDestroy(graph);
         if (ix && ix->graph) cudaGraphExecDestroy(ix->graph);
@@ -58,12 +57,12 @@ __global__ void fill_f32_kernel(float* __restrict__ x, int64_t n, float v) {
 // End of a batched iteration: another one runs while some problem has not
 // converged and fewer than max_iter iterations have run in this solve.
 __global__ void batch_cond_kernel(cudaGraphConditionalHandle h, int n, const life_sbb_state* __restrict__ st,
-                                  int64_t max_iter, int64_t* __restrict__ loops) {
+                                  int64_t* __restrict__ loop) {
     if (threadIdx.x != 0) return;
     bool any = false;
     for (int p = 0; p < n; ++p) any = any || !st[p].converged;
-    const int64_t k = ++(*loops);
-    cudaGraphSetConditional(h, (any && k < max_iter) ? 1u : 0u);
+    const int64_t k = ++loop[0];
+    cudaGraphSetConditional(h, (any && k < loop[1]) ? 1u : 0u);
 }
 
 template <class T>
@@ -415,6 +414,28 @@ extern "C" life_status life_batch_workspace_bytes(life_batch batch, size_t* byte
     return LIFE_OK;
 }
 
+namespace life {
+
+struct BatchSolveCtx {
+    life_index_s* ix;
+    const float* D;
+    life_sbb_state* st;
+    const BatchWork* W;
+    double tol;
+    int eq7;
+    int n;
+};
+
+static life_status enqueue_batch_round(void* p, cudaStream_t s, cudaGraphConditionalHandle h) {
+    BatchSolveCtx* c = static_cast<BatchSolveCtx*>(p);
+    LIFE_TRY(sbb_enqueue_batch_step(c->ix, c->D, c->st, *c->W, c->tol, c->eq7, s));
+    batch_cond_kernel<<<1, 32, 0, s>>>(h, c->n, c->st, c->W->loops);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+}  // namespace life
+
 extern "C" life_status life_batch_solve(life_batch batch, const float* D, const float* const* b, float* const* w,
                                         int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
                                         void* workspace, void* stream) {
@@ -446,56 +467,19 @@ extern "C" life_status life_batch_solve(life_batch batch, const float* D, const 
     }
     const void* key[3] = {D, st, workspace};
     const bool same = batch->graph && batch->graph_tol == tol && batch->graph_eq7 == eq7_on_even &&
-                      batch->graph_max_iter == max_iter && std::memcmp(key, batch->graph_key, sizeof(key)) == 0;
+                      std::memcmp(key, batch->graph_key, sizeof(key)) == 0;
     if (!same) {
         if (batch->graph) {
             cudaGraphExecDestroy(batch->graph);
             batch->graph = nullptr;
         }
-        cudaGraph_t g = nullptr;
-        LIFE_CUDA_TRY(cudaGraphCreate(&g, 0));
-        cudaGraphConditionalHandle h;
-        cudaError_t ce = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-        cudaGraphNodeParams cp = {};
-        cudaGraphNode_t node;
-        if (ce == cudaSuccess) {
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = h;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            ce = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
-        }
-        life_status est = LIFE_OK;
-        if (ce == cudaSuccess) {
-            // Capture the loop body on a private stream (the caller's may be the legacy default stream).
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            cudaStream_t cap;
-            ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-            if (ce == cudaSuccess) {
-                ce = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-                if (ce == cudaSuccess) {
-                    est = sbb_enqueue_batch_step(ix, D, st, W, tol, eq7_on_even, cap);
-                    batch_cond_kernel<<<1, 32, 0, cap>>>(h, n, st, max_iter, W.loops);
-                    cudaError_t le = cudaGetLastError();
-                    ce = cudaStreamEndCapture(cap, &body);
-                    if (ce == cudaSuccess) ce = le;
-                }
-                cudaStreamDestroy(cap);
-            }
-        }
-        if (est == LIFE_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&batch->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (est != LIFE_OK || ce != cudaSuccess) {
-            batch->graph = nullptr;
-            if (est == LIFE_OK) set_error("life_batch_solve: building the solve graph failed: %s", cudaGetErrorString(ce));
-            return est != LIFE_OK ? est : LIFE_ECUDA;
-        }
+        BatchSolveCtx c{ix, D, st, &W, tol, eq7_on_even, n};
+        LIFE_TRY(build_while_graph(enqueue_batch_round, &c, &batch->graph));
         std::memcpy(batch->graph_key, key, sizeof(key));
         batch->graph_tol = tol;
         batch->graph_eq7 = eq7_on_even;
-        batch->graph_max_iter = max_iter;
     }
-    LIFE_CUDA_TRY(cudaMemsetAsync(W.loops, 0, sizeof(int64_t), s));
+    LIFE_TRY(enqueue_loop_init(W.loops, max_iter, s));
     LIFE_CUDA_TRY(cudaGraphLaunch(batch->graph, s));
     for (int p = 0; p < n; ++p) {
         const size_t nf = bi.fasc_off[p + 1] - bi.fasc_off[p];

@@ -344,57 +344,48 @@ extern "C" life_status life_sbbnnls_step(life_index idx, const float* D, const f
     return sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, (cudaStream_t)stream);
 }
 
+namespace life {
+
+struct SolveCtx {
+    life_index_s* ix;
+    const float *D, *b;
+    float* w;
+    life_sbb_state* st;
+    void* ws;
+    double tol;
+    int eq7;
+};
+
+static life_status enqueue_solve_round(void* p, cudaStream_t s, cudaGraphConditionalHandle h) {
+    SolveCtx* c = static_cast<SolveCtx*>(p);
+    LIFE_TRY(sbb_enqueue_step(c->ix, c->D, c->b, c->w, c->st, c->ws, c->tol, c->eq7, s));
+    return enqueue_sbb_cond(h, c->st, sbb_loop_counter(c->ix, c->ws), s);
+}
+
+}  // namespace life
+
 extern "C" life_status life_sbbnnls_solve(life_index idx, const float* D, const float* b, float* w,
                                           int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
                                           void* workspace, void* stream) {
     LIFE_TRY(check_sbb_args(idx, D, b, w, st, workspace, "life_sbbnnls_solve"));
     if (max_iter <= 0) return LIFE_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const void* key[8] = {D, b, w, st, workspace, stream, nullptr, nullptr};
-    bool same = idx->graph && idx->graph_tol == tol && idx->graph_eq7 == eq7_on_even &&
-                std::memcmp(key, idx->graph_key, sizeof(key)) == 0;
+    const void* key[8] = {D, b, w, st, workspace, nullptr, nullptr, nullptr};
+    const bool same = idx->graph && idx->graph_tol == tol && idx->graph_eq7 == eq7_on_even &&
+                      std::memcmp(key, idx->graph_key, sizeof(key)) == 0;
     if (!same) {
         if (idx->graph) {
             cudaGraphExecDestroy(idx->graph);
             idx->graph = nullptr;
         }
-        // Capture on a private stream so that a caller on the legacy default
-        // stream can still use the graph.
-        cudaStream_t cap;
-        LIFE_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        LIFE_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        life_status est = sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, cap);
-        cudaError_t ce = cudaStreamEndCapture(cap, &g);
-        cudaStreamDestroy(cap);
-        if (est != LIFE_OK) {
-            if (g) cudaGraphDestroy(g);
-            return est;
-        }
-        if (ce != cudaSuccess) {
-            set_error("life_sbbnnls_solve: graph capture failed: %s", cudaGetErrorString(ce));
-            return LIFE_ECUDA;
-        }
-        cudaError_t ie = cudaGraphInstantiate(&idx->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (ie != cudaSuccess) {
-            idx->graph = nullptr;
-            set_error("life_sbbnnls_solve: graph instantiate failed: %s", cudaGetErrorString(ie));
-            return LIFE_ECUDA;
-        }
+        SolveCtx c{idx, D, b, w, st, workspace, tol, eq7_on_even};
+        LIFE_TRY(build_while_graph(enqueue_solve_round, &c, &idx->graph));
         std::memcpy(idx->graph_key, key, sizeof(key));
         idx->graph_tol = tol;
         idx->graph_eq7 = eq7_on_even;
     }
-    life_sbb_state hst;
-    for (int64_t i = 0; i < max_iter; ++i) {
-        LIFE_CUDA_TRY(cudaGraphLaunch(idx->graph, s));
-        if (tol > 0.0 && ((i + 1) % 64) == 0 && i + 1 < max_iter) {
-            LIFE_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
-            LIFE_CUDA_TRY(cudaStreamSynchronize(s));
-            if (hst.converged) break;
-        }
-    }
+    LIFE_TRY(enqueue_loop_init(sbb_loop_counter(idx, workspace), max_iter, s));
+    LIFE_CUDA_TRY(cudaGraphLaunch(idx->graph, s));
     return LIFE_OK;
 }
 
@@ -423,6 +414,52 @@ life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s) {
     }
     bounded_wait_probe_kernel<<<1, 32, 0, s>>>(status, (uint64_t)limit_ns);
     LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+}  // namespace life
+
+namespace life {
+
+life_status build_while_graph(while_body_fn enqueue_body, void* ctx, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    LIFE_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ce == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ce = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    life_status est = LIFE_OK;
+    if (ce == cudaSuccess) {
+        // Capture the body on a private stream (the caller's may be the legacy default stream).
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t cap;
+        ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) {
+            ce = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                est = enqueue_body(ctx, cap, h);
+                cudaError_t le = cudaGetLastError();
+                ce = cudaStreamEndCapture(cap, &body);
+                if (ce == cudaSuccess) ce = le;
+            }
+            cudaStreamDestroy(cap);
+        }
+    }
+    if (est == LIFE_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (est != LIFE_OK || ce != cudaSuccess) {
+        *out = nullptr;
+        if (est == LIFE_OK) set_error("building the solve graph failed: %s", cudaGetErrorString(ce));
+        return est != LIFE_OK ? est : LIFE_ECUDA;
+    }
     return LIFE_OK;
 }
 

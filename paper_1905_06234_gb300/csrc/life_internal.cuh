@@ -263,6 +263,19 @@ life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int
 life_status autotune_tc(life_index_s* ix, cudaStream_t s);
 int wc_effective_groups(const life_index_s* ix);
 life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s);
+
+// Builds and instantiates a graph made of one conditional WHILE node whose body
+// `enqueue_body(stream, handle)` captures (on a private stream).  The condition
+// starts at 1 at every launch; the body's last kernel sets it for the next round.
+typedef life_status (*while_body_fn)(void* ctx, cudaStream_t s, cudaGraphConditionalHandle h);
+life_status build_while_graph(while_body_fn enqueue_body, void* ctx, cudaGraphExec_t* out);
+// Loop control of a solve graph: loop[0] counts the rounds of a launch, loop[1]
+// holds the round limit; both are set by enqueue_loop_init before each launch.
+life_status enqueue_loop_init(int64_t* loop, int64_t max_iter, cudaStream_t s);
+// Ends a single-problem solve round: continue while the state has not converged
+// and fewer than loop[1] rounds ran.
+life_status enqueue_sbb_cond(cudaGraphConditionalHandle h, const life_sbb_state* st, int64_t* loop, cudaStream_t s);
+int64_t* sbb_loop_counter(const life_index_s* ix, void* workspace);
 // Per-problem launch maps of a batch's combined index (after its layouts are built).
 life_status batch_finalize(life_index_s* ix, cudaStream_t s);
 
@@ -271,7 +284,7 @@ life_status batch_finalize(life_index_s* ix, cudaStream_t s);
 struct BatchWork {
     float *b, *e, *w, *g, *gt, *u;  // combined signal / residual [Nθ·Nv], weights and gradients [Nf]
     int32_t* live;                  // [n]
-    int64_t* loops;                 // solve-loop counter
+    int64_t* loops;                 // solve-loop control: [0] rounds run, [1] round limit
     double *pe, *pv, *pg, *pu;      // per-problem partial sums
 };
 size_t batch_workspace_bytes(const life_index_s* ix);

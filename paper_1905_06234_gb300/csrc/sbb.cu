@@ -251,7 +251,37 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t sbb_workspace_bytes(const life_index_s* ix) {
     const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf;
-    return align256(ny * 4) + 3 * align256(nf * 4) + 4 * align256(RED_SLOTS * 8);
+    return align256(ny * 4) + 3 * align256(nf * 4) + 4 * align256(RED_SLOTS * 8) + align256(16);
+}
+
+// The solve graph's loop control sits after the other workspace arrays:
+// [0] rounds run in this launch, [1] the round limit (max_iter).
+int64_t* sbb_loop_counter(const life_index_s* ix, void* ws) {
+    return reinterpret_cast<int64_t*>(static_cast<char*>(ws) + sbb_workspace_bytes(ix) - align256(16));
+}
+
+__global__ void loop_init_kernel(int64_t* loop, int64_t max_iter) {
+    loop[0] = 0;
+    loop[1] = max_iter;
+}
+
+life_status enqueue_loop_init(int64_t* loop, int64_t max_iter, cudaStream_t s) {
+    loop_init_kernel<<<1, 1, 0, s>>>(loop, max_iter);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+__global__ void sbb_cond_kernel(cudaGraphConditionalHandle h, const life_sbb_state* __restrict__ st,
+                                int64_t* __restrict__ loop) {
+    if (threadIdx.x != 0) return;
+    const int64_t k = ++loop[0];
+    cudaGraphSetConditional(h, (!st->converged && k < loop[1]) ? 1u : 0u);
+}
+
+life_status enqueue_sbb_cond(cudaGraphConditionalHandle h, const life_sbb_state* st, int64_t* loop, cudaStream_t s) {
+    sbb_cond_kernel<<<1, 32, 0, s>>>(h, st, loop);
+    LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
 }
 
 static SbbWork carve(const life_index_s* ix, void* ws) {
@@ -420,7 +450,7 @@ size_t batch_workspace_bytes(const life_index_s* ix) {
     const BatchInfo& bi = ix->batch;
     const size_t ny = (size_t)ix->nt * ix->nv, nf = ix->nf, n = bi.n;
     const size_t np = std::max<size_t>(bi.part_off.empty() ? 1 : bi.part_off.back(), 1);
-    return 2 * align256(ny * 4) + 4 * align256(nf * 4) + align256(n * 4) + align256(8) + 2 * align256(np * 8) +
+    return 2 * align256(ny * 4) + 4 * align256(nf * 4) + align256(n * 4) + align256(16) + 2 * align256(np * 8) +
            2 * align256(n * BATCH_VGX * 8);
 }
 
@@ -437,7 +467,7 @@ BatchWork batch_carve(const life_index_s* ix, void* ws) {
     W.gt = reinterpret_cast<float*>(p); p += align256(nf * 4);
     W.u = reinterpret_cast<float*>(p); p += align256(nf * 4);
     W.live = reinterpret_cast<int32_t*>(p); p += align256(n * 4);
-    W.loops = reinterpret_cast<int64_t*>(p); p += align256(8);
+    W.loops = reinterpret_cast<int64_t*>(p); p += align256(16);
     W.pe = reinterpret_cast<double*>(p); p += align256(np * 8);
     W.pv = reinterpret_cast<double*>(p); p += align256(np * 8);
     W.pg = reinterpret_cast<double*>(p); p += align256(n * BATCH_VGX * 8);
