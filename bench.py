@@ -256,8 +256,9 @@ def e2e_steps(life, path, steps, warmup):
 
 def launches_per_step(path):
     # DSC + WC + project + scalars + DSC + WC + sumsq + scalars + update, and on the
-    # tensor-core path the brick weight gather before each of the two DSCs
-    return 11 if path.info["algo"] == 2 else 9
+    # tensor-core path the brick weight gather before each of the two DSCs and the
+    # per-brick max |r| pass before each of the two WCs
+    return 13 if path.info["algo"] == 2 else 9
 
 
 def max_over_ranks(value, dist, device):

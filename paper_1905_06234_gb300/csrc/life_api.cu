@@ -224,7 +224,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
                             &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
                             &idx->tile.va, &idx->tile.soff, &idx->tile.fl, &idx->tile.val, &idx->tile.wkey,
                             &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->tile.wb_src,
-                            &idx->tile.wb_ptr, &idx->tile.wb, &idx->red};
+                            &idx->tile.wb_ptr, &idx->tile.wb, &idx->tile.brick_cv, &idx->tile.tile_amax, &idx->red};
     int64_t tot = 0;
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;

@@ -156,6 +156,10 @@ struct TileLayout {
     DevBuf wb_src;           // int32 [wb_total]: global fascicle of each slot (0 for padding)
     DevBuf wb_ptr;           // int32 [n_bricks + 1], multiples of 4
     DevBuf wb;               // float [wb_total]: gathered weights (rewritten by every DSC call)
+    // WC fixed-point tables: per brick, an upper bound on Σ|val| over the entries of
+    // any one brick-local fascicle; per tile, the bits of max |r| over its voxels
+    DevBuf brick_cv;         // float [n_bricks]: (largest entry count of a fascicle) x (largest |val|)
+    DevBuf tile_amax;        // uint32 [n_tiles]: bits of max |r| (rewritten by every WC call)
 };
 
 // A block-diagonal index that concatenates several problems (batched solve):

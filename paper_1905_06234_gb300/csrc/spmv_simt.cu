@@ -8,6 +8,7 @@
 // products with a transpose-reduction of shuffles and adds val·dot into g[f]
 // with one atomic per nonzero (the paper's coefficient-based WC also uses atomics).
 #include "life_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace life {
 
@@ -233,7 +234,7 @@ wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__
                 part[j] = p;
             }
             const float dot = transpose_reduce32(part, lane);
-            if (k < end) atomicAdd(g + fasc[k], ldval<VT>(val, k) * dot);
+            if (k < end) ptx::red_add_global_f32(g + fasc[k], ldval<VT>(val, k) * dot);
         }
     }
 }

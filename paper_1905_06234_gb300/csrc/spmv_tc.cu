@@ -118,6 +118,40 @@ __global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, co
     }
 }
 
+// cv[b] = (largest number of WC entries of one brick-local fascicle of brick b) x
+// (largest |val| of the brick), rounded up: it bounds Σ|val| over the entries of
+// any fascicle of the brick.  Integer counts and maxima, so the result does not
+// depend on the order of the atomics.  Dynamic shared memory: max_fb counters.
+__global__ void brick_cv_kernel(const int32_t* __restrict__ btile, const int32_t* __restrict__ bfptr,
+                                const int32_t* __restrict__ wseg_ptr, int32_t seg_per_tile,
+                                const uint16_t* __restrict__ wfl, const __nv_bfloat16* __restrict__ wval,
+                                int32_t nb, float* __restrict__ cv) {
+    extern __shared__ int32_t cnt[];
+    __shared__ uint32_t vmax_bits, cmax;
+    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int32_t nfb = bfptr[b + 1] - bfptr[b];
+        for (int32_t i = threadIdx.x; i < nfb; i += blockDim.x) cnt[i] = 0;
+        if (threadIdx.x == 0) vmax_bits = cmax = 0u;
+        __syncthreads();
+        const int32_t j0 = wseg_ptr[(int64_t)btile[b] * seg_per_tile], j1 = wseg_ptr[(int64_t)btile[b + 1] * seg_per_tile];
+        uint32_t vm = 0u;
+        for (int32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            atomicAdd(&cnt[wfl[j]], 1);
+            vm = max(vm, __float_as_uint(__bfloat162float(wval[j])) & 0x7FFFFFFFu);
+        }
+        for (int o = 16; o > 0; o >>= 1) vm = max(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&vmax_bits, vm);
+        __syncthreads();
+        uint32_t cm = 0u;
+        for (int32_t i = threadIdx.x; i < nfb; i += blockDim.x) cm = max(cm, (uint32_t)cnt[i]);
+        for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&cmax, cm);
+        __syncthreads();
+        if (threadIdx.x == 0) cv[b] = __fmul_ru((float)cmax, __uint_as_float(vmax_bits));
+        __syncthreads();
+    }
+}
+
 // Brick-local fascicle number of each entry, scattered back to tile order.
 // uidx is the exclusive scan of the head flags, so an entry that repeats its
 // predecessor's (brick, fascicle) belongs to unique index uidx - 1.
@@ -476,6 +510,16 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     }
     LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
     LIFE_TRY(upload(L.brick_tile_ptr, H.brick_tile_ptr, s));
+    LIFE_TRY(L.brick_cv.alloc(sizeof(float) * std::max<int64_t>(H.n_bricks, 1)));
+    LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * std::max<int64_t>(H.n_tiles, 1)));
+    if (H.n_bricks > 0) {
+        const int cv_smem = (int)sizeof(int32_t) * std::max(L.max_fb, 1);
+        LIFE_CUDA_TRY(cudaFuncSetAttribute(brick_cv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cv_smem));
+        brick_cv_kernel<<<(unsigned)std::min<int64_t>(H.n_bricks, 65535), 256, cv_smem, s>>>(
+            L.brick_tile_ptr.as<int32_t>(), L.brick_fasc_ptr.as<int32_t>(), L.wseg_ptr.as<int32_t>(), 4 * L.n_sub,
+            L.wfl.as<uint16_t>(), L.wval.as<__nv_bfloat16>(), (int32_t)H.n_bricks, L.brick_cv.as<float>());
+        LIFE_CHECK_LAUNCH();
+    }
     // largest bricks first
     std::vector<int32_t> tptr(H.n_tiles + 1);
     {
@@ -550,6 +594,8 @@ struct TcArgs {
     double* partial;     // DSC: per-CTA FP64 Σ out²
     const float* wb;     // DSC: gathered brick weight tables
     const int32_t* wb_ptr;
+    const float* brick_cv;    // WC: per-brick bound on Σ|val| of one fascicle
+    uint32_t* tile_amax;      // WC: per-tile bits of max |r|
     const life_sbb_state* gate;
     int gate_mode;
     uint32_t* status;
@@ -632,8 +678,9 @@ __device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int 
 }
 
 // dst[idx[i]] += tab[i] for every non-zero tab[i], i < n (one atomic per fascicle).
+// With inv != 0 the table holds int32 values in units of inv.
 __device__ __forceinline__ void flush_table(float* dst, const float* tab, const int32_t* __restrict__ idx, int n,
-                                            int tid, int nthr) {
+                                            int tid, int nthr, float inv = 0.0f) {
     for (int b0 = 0; b0 < n; b0 += 8 * nthr) {
         int id[8];
         float v[8];
@@ -641,17 +688,18 @@ __device__ __forceinline__ void flush_table(float* dst, const float* tab, const 
         for (int e = 0; e < 8; ++e) {
             const int i = b0 + e * nthr + tid;
             v[e] = i < n ? tab[i] : 0.0f;
+            if (inv != 0.0f) v[e] = (float)__float_as_int(v[e]) * inv;
             id[e] = (i < n && v[e] != 0.0f) ? __ldg(idx + i) : -1;
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-            if (id[e] >= 0) atomicAdd(dst + id[e], v[e]);
+            if (id[e] >= 0) red_add_global_f32(dst + id[e], v[e]);
     }
 }
 
 // ---------------------------------------------------------------------- DSC
 
-constexpr int DSC_PROD_WARPS = 19;   // 24 warps in all: 6 per SM sub-partition fit 80 registers
+constexpr int DSC_PROD_WARPS = 23;   // 28 warps in all: 7 per SM sub-partition fit 72 registers
 constexpr int DSC_EPI_WARPS = 4;
 constexpr int DSC_MMA_WARP = DSC_PROD_WARPS + DSC_EPI_WARPS;
 constexpr int DSC_THREADS = (DSC_MMA_WARP + 1) * 32;
@@ -743,7 +791,7 @@ __device__ __forceinline__ void dsc_flush_sq(const TcArgs& A, double& sq, int p,
     sq = 0.0;
 }
 
-__global__ void __maxnreg__(80) dsc_tc_kernel(TcArgs A) {
+__global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
         tab_bar;
@@ -1070,8 +1118,11 @@ __host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, in
     return d + r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
-template <bool CHECK>
-__device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Zw, float* gl) {
+// FIXED: the table holds 32-bit integers in units of 1/sc (sc a power of two chosen
+// so that no partial sum can leave the int32 range); otherwise FP32.
+template <bool CHECK, bool FIXED>
+__device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Zw,
+                                          float* gl, uint32_t gl_s, float sc) {
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
         if (CHECK) {
@@ -1079,8 +1130,17 @@ __device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg,
             if (idx < beg || idx >= end) continue;
         }
         const uint32_t k = u16_at(s.key, e);
-        atomicAdd(&gl[u16_at(s.fl, e)], bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)]);
+        const float x = bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)];
+        if (FIXED) atomicAdd(reinterpret_cast<int*>(gl) + u16_at(s.fl, e), __float2int_rn(x * sc));
+        else red_add_shared_f32(gl_s + 4u * u16_at(s.fl, e), x);
     }
+}
+
+template <bool FIXED>
+__device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Zw, float* gl,
+                                        uint32_t gl_s, float sc) {
+    if (base >= beg && base + SLOT <= end) wc_slot_t<false, FIXED>(s, base, beg, end, Zw, gl, gl_s, sc);
+    else wc_slot_t<true, FIXED>(s, base, beg, end, Zw, gl, gl_s, sc);
 }
 
 __device__ __forceinline__ void wc_load_slot(const TcArgs& A, int base, EntrySlot& s) {
@@ -1093,10 +1153,66 @@ __device__ __forceinline__ int wseg(const TcArgs& A, int t, int q, int s) {
     return A.wseg_ptr[((int64_t)t * 4 + q) * A.n_sub + s];
 }
 
+// tile_amax[t] = bits of max |r[θ, v]| over the voxels v of tile t (the bits order
+// non-negative floats, and NaN above +inf), for the tiles of the bricks the WC
+// launch works on.  One block per tile; the row voxel ids are staged in shared
+// memory so that the loads of r are independent of one another.
+constexpr int AMAX_THREADS = 256;
+
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+
+__global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
+    __shared__ int32_t tv[TILE_V];
+    __shared__ uint32_t wmax[AMAX_THREADS / 32];
+    if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
+    const int tid = threadIdx.x;
+    const int n_tiles = A.brick_tile_ptr[A.n_bricks];
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        if (A.bg.live) {
+            int lo = 0, hi = A.n_bricks - 1;  // the brick of tile t: last brick starting at or before t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.brick_tile_ptr[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            if (!batch_live(A.bg, A.bg.brick_prob[lo], A.gate_mode)) continue;
+        }
+        if (tid < TILE_V) tv[tid] = A.tile_vox[(int64_t)t * TILE_V + tid];
+        __syncthreads();
+        uint32_t m = 0u;
+        if (A.vec4) {
+            const int q4 = A.nt >> 2, n = TILE_V * q4;
+#pragma unroll 4
+            for (int i = tid; i < n; i += AMAX_THREADS) {
+                const int row = i / q4, c = i - row * q4, v = tv[row];
+                if (v >= 0) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(A.x + (int64_t)A.nt * v) + c);
+                    m = max(max(m, max(abs_bits(x.x), abs_bits(x.y))), max(abs_bits(x.z), abs_bits(x.w)));
+                }
+            }
+        } else {
+            const int n = TILE_V * A.nt;
+#pragma unroll 4
+            for (int i = tid; i < n; i += AMAX_THREADS) {
+                const int row = i / A.nt, c = i - row * A.nt, v = tv[row];
+                if (v >= 0) m = max(m, abs_bits(__ldg(A.x + (int64_t)A.nt * v + c)));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) wmax[tid >> 5] = m;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t x = wmax[0];
+            for (int i = 1; i < AMAX_THREADS / 32; ++i) x = max(x, wmax[i]);
+            A.tile_amax[t] = x;
+        }
+    }
+}
+
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t r_full, r_empty, z_full, z_empty, fin_bar;
-    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t tmem_base, d1_bits;
     __shared__ int abort_flag, never;
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1125,6 +1241,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         mbar_init(&fin_bar, 1);
         abort_flag = 0;
         never = 0;
+        d1_bits = 0u;
         fence_barrier_init();
     }
     if (warp == WC_MMA_WARP) {
@@ -1137,17 +1254,46 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     tc_fence_after();
     const uint32_t tb = tmem_base;
     const int G = gridDim.x, cta = blockIdx.x;
+    {
+        // max over atoms of Σθ |D[θ, a]| for the BF16 D the MMA reads (one warp per
+        // atom; a NaN column sum gives bits above those of +inf)
+        uint32_t m = 0u;
+        for (int a = warp; a < A.na; a += WC_THREADS / 32) {
+            float sum = 0.0f;
+            for (int t = lane; t < A.np; t += 32)
+                sum += fabsf(__bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(Dw + kmajor_off(a, t, SBO_K))));
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            m = max(m, __float_as_uint(sum) & 0x7FFFFFFFu);
+        }
+        if (lane == 0 && m != 0u) atomicMax(&d1_bits, m);
+    }
+    __syncthreads();
 
     if (warp < WC_SCAT_WARPS) {
         const int q = warp & 3, h = warp >> 2;
         const bool active = h < wg;               // warps beyond wgroups groups only keep step
         float* Zw = Zc + (active ? (h * 4 + q) : 0) * (ZW_BYTES / 4);
+        const uint32_t gl_s = smem_u32(gl);
         uint32_t tcount = 0;
         bool dead = false;
         for (int r = 0;; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
             const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
+            // Fixed point: every entry adds val·Z with |val·Z| <= max|val|·max_a Σθ|D|·max|r|
+            // (up to the BF16 roundings of r and D, < 1 %), and a fascicle has at most
+            // cnt entries in the brick, so |any partial sum| <= cv·d1·rmax = bnd.  With
+            // sc = 2^(29 - e), bnd < 2^e, a table word stays below 2^29·1.01 + cnt/2 < 2^31.
+            // Non-finite or tiny bounds keep the FP32 table.
+            uint32_t am = 0u;
+            for (int t = A.brick_tile_ptr[brick] + lane; t < A.brick_tile_ptr[brick + 1]; t += 32)
+                am = max(am, A.tile_amax[t]);
+            for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+            const float bnd = A.brick_cv[brick] * __uint_as_float(d1_bits) * __uint_as_float(am);
+            int bexp = 0;
+            (void)frexpf(bnd, &bexp);
+            const bool fixed = bnd <= 3.0e38f && bnd >= 1.0e-27f;
+            const float sc = fixed ? ldexpf(1.0f, 29 - bexp) : 0.0f, inv = fixed ? ldexpf(1.0f, bexp - 29) : 0.0f;
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
             for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
             named_bar_sync(2, WC_SCAT_THREADS);
@@ -1195,8 +1341,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                                 wc_load_slot(A, nbase, nxt);
                                 pf = true;
                             }
-                            if (base >= beg && base + SLOT <= end) wc_slot_t<false>(cur, base, beg, end, Zw, gl);
-                            else wc_slot_t<true>(cur, base, beg, end, Zw, gl);
+                            if (fixed) wc_slot<true>(cur, base, beg, end, Zw, gl, gl_s, sc);
+                            else wc_slot<false>(cur, base, beg, end, Zw, gl, gl_s, sc);
                             if (!more) break;
                             cur = nxt;
                             base = b2;
@@ -1217,7 +1363,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                 if (lane == 0) mbar_arrive(&z_empty);  // this warp is done with the tile's TMEM
             }
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
-            flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS);
+            flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS, inv);
         }
     } else if (warp < WC_MMA_WARP) {
         // ---------------- R tile loader: r[:, v] -> bf16 A operand (rows = voxels, K = θ)
@@ -1359,6 +1505,8 @@ static TcArgs make_args(life_index_s* ix) {
     A.val = L.val.as<__nv_bfloat16>();
     A.wb = L.wb.as<float>();
     A.wb_ptr = L.wb_ptr.as<int32_t>();
+    A.brick_cv = L.brick_cv.as<float>();
+    A.tile_amax = L.tile_amax.as<uint32_t>();
     A.nt = ix->nt;
     A.na = ix->na;
     A.np = L.np;
@@ -1422,6 +1570,10 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     }
     const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
     LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (ix->tile.n_tiles > 0) {
+        wc_amax_kernel<<<(unsigned)std::min<int64_t>(ix->tile.n_tiles, (int64_t)ix->num_sms * 8), AMAX_THREADS, 0, s>>>(A);
+        LIFE_CHECK_LAUNCH();
+    }
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
     wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();

@@ -17,6 +17,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Adds x to the FP32 word at shared-memory address addr (no return value).  The
+// explicit shared-space reduction is much cheaper than an atomicAdd through a
+// generic pointer.
+__device__ __forceinline__ void red_add_shared_f32(uint32_t addr, float x) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(x) : "memory");
+}
+
+// Adds x to the FP32 word at p, which points into device global memory.
+__device__ __forceinline__ void red_add_global_f32(float* p, float x) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(x) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }

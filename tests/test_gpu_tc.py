@@ -236,3 +236,93 @@ def test_tc_layout_bit_exact(life, use_ijk):
             tv = got["tile_vox"][128 * got["brick_tile_ptr"][bi]:128 * got["brick_tile_ptr"][bi + 1]]
             ijk = p.voxel_ijk[tv[tv >= 0]] // B
             assert (ijk == ijk[0]).all()
+
+
+def fixed_point_bound(phi, D32, r, tile_vox, brick_tile_ptr, nt, nv, nf):
+    """Per-fascicle bound on the extra error of WC's fixed-point brick tables.
+
+    Each entry's product val*Z is rounded to a multiple of the brick's unit
+    2^(e-29), where bnd = cnt * vmax * d1 * rmax < 2^e is the brick's bound on any
+    fascicle's sum (cnt: most entries of one fascicle in the brick, vmax: largest
+    |val|, d1: largest column sum of |D| in BF16, rmax: largest |r| over the
+    brick's voxels).  Half a unit is below 2^-29 * bnd, once per entry."""
+    import torch as _t
+    tile_brick = np.repeat(np.arange(len(brick_tile_ptr) - 1), np.diff(brick_tile_ptr))
+    vox_brick = np.full(nv, -1, np.int64)
+    rows = np.nonzero(tile_vox >= 0)[0]
+    vox_brick[tile_vox[rows]] = tile_brick[rows // 128]
+    nb = len(brick_tile_ptr) - 1
+    eb = vox_brick[phi.voxel]
+    valb = np.abs(_t.from_numpy(phi.val).to(_t.bfloat16).float().numpy()).astype(np.float64)
+    Db = np.abs(_t.from_numpy(D32).to(_t.bfloat16).float().numpy()).astype(np.float64).reshape(-1, nt)
+    d1 = Db.sum(axis=1).max()
+    cnt = np.zeros(nb)
+    key, c = np.unique(eb * (nf + 1) + phi.fasc, return_counts=True)
+    np.maximum.at(cnt, key // (nf + 1), c)
+    vmax = np.zeros(nb)
+    np.maximum.at(vmax, eb, valb)
+    rmax = np.zeros(nb)
+    placed = vox_brick >= 0
+    np.maximum.at(rmax, vox_brick[placed], np.abs(r.reshape(nv, nt)[placed]).max(axis=1).astype(np.float64))
+    bnd = cnt * vmax * d1 * rmax
+    return np.bincount(phi.fasc, weights=2.0 ** -29 * bnd[eb], minlength=nf)
+
+
+def tiny_case(life):
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    idx = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                   p.n_fasc, ijk=p.voxel_ijk)
+    return p, D32, phi, idx
+
+
+def test_wc_fixed_point_outlier(life):
+    """One voxel's residual 1e5 times the rest: that brick's fixed-point unit is
+    set by the outlier, and every fascicle still lands within the BF16 rounding
+    bound plus the fixed-point bound (a scale that overflowed the int32 tables or
+    was too coarse would break it)."""
+    p, D32, phi, idx = tiny_case(life)
+    nt, nv, nf = p.n_theta, p.n_voxels, p.n_fasc
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(nt * nv).astype(np.float32)
+    hot = int(phi.voxel[len(phi.voxel) // 2])
+    r[hot * nt:(hot + 1) * nt] *= 1e5
+    g, _ = life.life_wc(idx, dev(D32), dev(r))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    g = g.cpu().numpy()
+    g_ref = oracle.wc(phi, D32, r, nt, nf)
+    tiles = {k: v.cpu().numpy() for k, v in life.life_index_export_tiles(idx).items()}
+    n_tiles = idx.info()["n_tiles"]
+    fxb = fixed_point_bound(phi, D32, r, tiles["tile_vox"][:128 * n_tiles], tiles["brick_tile_ptr"], nt, nv, nf)
+    _, gb = rounding_bounds(phi, D32, np.zeros(nf, np.float32), r, nt, nv, nf)
+    assert (np.abs(g - g_ref) <= gb + fxb + 1e-30).all(), float((np.abs(g - g_ref) / (gb + fxb + 1e-30)).max())
+    assert rel(g, g_ref) <= TOL_BF16
+
+
+def test_wc_non_finite_residual(life):
+    """A NaN in one voxel's residual and +inf in another's: the fascicles through
+    them come out NaN / infinite exactly as in the FP64 oracle (their bricks keep
+    FP32 tables), and every other fascicle stays within the rounding bound."""
+    p, D32, phi, idx = tiny_case(life)
+    nt, nv, nf = p.n_theta, p.n_voxels, p.n_fasc
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(nt * nv).astype(np.float32)
+    vs = np.unique(phi.voxel)
+    r[int(vs[3]) * nt + 5] = np.nan
+    r[int(vs[-4]) * nt + 7] = np.inf
+    g, _ = life.life_wc(idx, dev(D32), dev(r))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    g = g.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        g_ref = oracle.wc(phi, D32, r, nt, nf)
+    np.testing.assert_array_equal(np.isnan(g), np.isnan(g_ref))
+    np.testing.assert_array_equal(np.isposinf(g), np.isposinf(g_ref))
+    np.testing.assert_array_equal(np.isneginf(g), np.isneginf(g_ref))
+    ok = np.isfinite(g_ref)
+    assert 0 < (~ok).sum() < nf
+    r0 = np.where(np.isfinite(r), r, 0.0).astype(np.float32)
+    _, gb = rounding_bounds(phi, D32, np.zeros(nf, np.float32), r0, nt, nv, nf)
+    assert (np.abs(g[ok] - g_ref[ok]) <= gb[ok] + 1e-30).all()
