@@ -58,7 +58,7 @@ __global__ void zero_f32_kernel(float* __restrict__ x, int64_t n) {
 }
 
 life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s, const BatchGate& bg) {
+                    int gate_mode, cudaStream_t s, const BatchGate& bg, bool r_is_dsc_out) {
     if (bg.live) {
         // a kernel rather than a memset, so the batched step is all kernel nodes
         zero_f32_kernel<<<ix->num_sms * 2, 256, 0, s>>>(g, ix->nf);
@@ -66,7 +66,7 @@ life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, 
     } else {
         LIFE_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * (size_t)ix->nf, s));
     }
-    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s, bg);
+    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s, bg, r_is_dsc_out);
     return wc_simt(ix, D, r, g, gate, gate_mode, s, bg);
 }
 

@@ -159,7 +159,8 @@ struct TileLayout {
     // WC fixed-point tables: per brick, an upper bound on Σ|val| over the entries of
     // any one brick-local fascicle; per tile, the bits of max |r| over its voxels
     DevBuf brick_cv;         // float [n_bricks]: (largest entry count of a fascicle) x (largest |val|)
-    DevBuf tile_amax;        // uint32 [n_tiles]: bits of max |r| (rewritten by every WC call)
+    DevBuf tile_amax;        // uint32 [n_tiles * 4]: bits of max |r| per tile row quarter (written by
+                             // every DSC that stores y, and by WC calls whose r did not come from one)
 };
 
 // A block-diagonal index that concatenates several problems (batched solve):
@@ -250,8 +251,10 @@ int simt_total_warps(const life_index_s* ix);
 life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float* b, float* y,
                    double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
                    cudaStream_t s, const BatchGate& bg = BatchGate());
+// r_is_dsc_out: r is the y that the last tensor-core DSC on this index wrote, so its
+// per-tile max |r| (written by that DSC's epilogue) is already in place.
 life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                  int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
+                  int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate(), bool r_is_dsc_out = false);
 
 // ------------------------------------------------------------- dispatch
 // DSC / WC on whichever kernels the index uses (WC zeroes g first).
@@ -259,7 +262,7 @@ life_status spmv_dsc(life_index_s* ix, const float* D, const float* w, const flo
                      int* n_partial, const life_sbb_state* gate, int gate_mode, cudaStream_t s,
                      const BatchGate& bg = BatchGate());
 life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
-                    int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate());
+                    int gate_mode, cudaStream_t s, const BatchGate& bg = BatchGate(), bool r_is_dsc_out = false);
 life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
                                 const float* val, const int32_t* voxel_ijk, int algo_req, cudaStream_t s);
 // Chooses brick_dim and wc_groups of a tensor-core index by timing candidates

@@ -310,7 +310,7 @@ life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, f
     // e = M w − b, Σ e²
     LIFE_TRY(spmv_dsc(ix, D, w, b, W.e, W.pe, &ne, st, GATE_ACTIVE, s));
     // g = M^T e
-    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s));
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s, BatchGate(), true));
     // g~, Σ g~²
     sbb_project_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, W.g, W.gt, nf, W.pg, st);
     LIFE_CHECK_LAUNCH();
@@ -319,7 +319,7 @@ life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, f
     // v' = M g~ (stored only on Eq. 8 iterations), Σ v'²
     LIFE_TRY(spmv_dsc(ix, D, W.gt, nullptr, W.e, W.pv, &nv_, st, 3, s));
     // v'' = M^T v', Σ v''² (Eq. 8 iterations only)
-    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s));
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s, BatchGate(), true));
     LIFE_TRY(sumsq_f32(W.u, nf, W.pu, &nu, st, GATE_EQ8, s));
     sbb_scalars2_kernel<<<1, RED_THREADS, 0, s>>>(st, W.pv, nv_, W.pu, nu);
     LIFE_CHECK_LAUNCH();
@@ -495,7 +495,7 @@ life_status sbb_enqueue_batch_step(life_index_s* ix, const float* D, life_sbb_st
     // e = M w − b, Σ e² per problem
     LIFE_TRY(spmv_dsc(ix, D, W.w, W.b, W.e, W.pe, nullptr, st, GATE_ACTIVE, s, bg));
     // g = M^T e
-    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s, bg));
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.g, st, GATE_ACTIVE, s, bg, true));
     batch_project_kernel<<<vgrid, RED_THREADS, 0, s>>>(W.w, W.g, W.gt, fasc_off, W.pg, W.live);
     LIFE_CHECK_LAUNCH();
     batch_scalars1_kernel<<<n, RED_THREADS, 0, s>>>(st, W.live, W.pe, part_off, W.pg, BATCH_VGX, tol, eq7_on_even);
@@ -503,7 +503,7 @@ life_status sbb_enqueue_batch_step(life_index_s* ix, const float* D, life_sbb_st
     // v' = M g~ (stored on Eq. 8 iterations), Σ v'²
     LIFE_TRY(spmv_dsc(ix, D, W.gt, nullptr, W.e, W.pv, nullptr, st, GATE_ACTIVE_Y_EQ8, s, bg));
     // v'' = M^T v', Σ v''² (Eq. 8 iterations)
-    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s, bg));
+    LIFE_TRY(spmv_wc(ix, D, W.e, W.u, st, GATE_EQ8, s, bg, true));
     batch_sumsq_kernel<<<vgrid, RED_THREADS, 0, s>>>(W.u, fasc_off, W.pu, W.live, st);
     LIFE_CHECK_LAUNCH();
     batch_scalars2_kernel<<<n, RED_THREADS, 0, s>>>(st, W.live, W.pv, part_off, W.pu, BATCH_VGX);

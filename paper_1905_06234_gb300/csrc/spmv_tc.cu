@@ -511,7 +511,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
     LIFE_TRY(upload(L.brick_tile_ptr, H.brick_tile_ptr, s));
     LIFE_TRY(L.brick_cv.alloc(sizeof(float) * std::max<int64_t>(H.n_bricks, 1)));
-    LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * std::max<int64_t>(H.n_tiles, 1)));
+    LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * 4 * std::max<int64_t>(H.n_tiles, 1)));
     if (H.n_bricks > 0) {
         const int cv_smem = (int)sizeof(int32_t) * std::max(L.max_fb, 1);
         LIFE_CUDA_TRY(cudaFuncSetAttribute(brick_cv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cv_smem));
@@ -595,7 +595,7 @@ struct TcArgs {
     const float* wb;     // DSC: gathered brick weight tables
     const int32_t* wb_ptr;
     const float* brick_cv;    // WC: per-brick bound on Σ|val| of one fascicle
-    uint32_t* tile_amax;      // WC: per-tile bits of max |r|
+    uint32_t* tile_amax;      // bits of max |r| per (tile, row quarter): written by DSC, read by WC
     const life_sbb_state* gate;
     int gate_mode;
     uint32_t* status;
@@ -625,6 +625,10 @@ __device__ __forceinline__ int live_brick(const TcArgs& A, int G, int cta, int& 
 }
 
 __device__ __forceinline__ uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Bits of |x|: they order non-negative floats, with +inf above every finite value
+// and NaN above +inf.
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 
 // Lane 0 waits (bounded) and the verdict is broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
@@ -978,6 +982,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 const int v = A.tile_vox[(int64_t)t * TILE_V + row];
                 const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + ab * 128u;
                 float sqf = 0.0f;
+                uint32_t am = 0u;  // bits of max |y| over this warp's rows (for a WC of y)
                 for (int j = 0; j < A.np; j += 32) {
                     uint32_t rr[32];
                     int cnt = 32;
@@ -1006,6 +1011,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                             }
                             if (wy) *reinterpret_cast<float4*>(A.out + o + e) = yv;
                             sqf += yv.x * yv.x + yv.y * yv.y + yv.z * yv.z + yv.w * yv.w;
+                            am = max(max(am, max(abs_bits(yv.x), abs_bits(yv.y))), max(abs_bits(yv.z), abs_bits(yv.w)));
                         }
                     } else {
                         for (int e = 0; e < cnt; ++e) {
@@ -1014,11 +1020,16 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                                 if (A.b) y -= A.b[o + e];
                                 if (wy) A.out[o + e] = y;
                                 sqf += y * y;
+                                am = max(am, abs_bits(y));
                             }
                         }
                     }
                 }
                 sq += (double)sqf;
+                if (wy) {
+                    for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+                    if (lane == 0) A.tile_amax[(int64_t)t * 4 + q] = am;
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[ab]);
@@ -1153,13 +1164,11 @@ __device__ __forceinline__ int wseg(const TcArgs& A, int t, int q, int s) {
     return A.wseg_ptr[((int64_t)t * 4 + q) * A.n_sub + s];
 }
 
-// tile_amax[t] = bits of max |r[θ, v]| over the voxels v of tile t (the bits order
-// non-negative floats, and NaN above +inf), for the tiles of the bricks the WC
-// launch works on.  One block per tile; the row voxel ids are staged in shared
+// tile_amax[4t .. 4t+3] = (bits of max |r[θ, v]| over the voxels v of tile t, 0, 0,
+// 0), for the tiles of the bricks the WC launch works on (a DSC that stores y
+// writes the same slots, one per row quarter).  One block per tile; the row voxel ids are staged in shared
 // memory so that the loads of r are independent of one another.
 constexpr int AMAX_THREADS = 256;
-
-__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 
 __global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
     __shared__ int32_t tv[TILE_V];
@@ -1204,7 +1213,7 @@ __global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
         if (tid == 0) {
             uint32_t x = wmax[0];
             for (int i = 1; i < AMAX_THREADS / 32; ++i) x = max(x, wmax[i]);
-            A.tile_amax[t] = x;
+            *reinterpret_cast<uint4*>(A.tile_amax + (int64_t)t * 4) = make_uint4(x, 0u, 0u, 0u);
         }
     }
 }
@@ -1286,8 +1295,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             // sc = 2^(29 - e), bnd < 2^e, a table word stays below 2^29·1.01 + cnt/2 < 2^31.
             // Non-finite or tiny bounds keep the FP32 table.
             uint32_t am = 0u;
-            for (int t = A.brick_tile_ptr[brick] + lane; t < A.brick_tile_ptr[brick + 1]; t += 32)
-                am = max(am, A.tile_amax[t]);
+            for (int i = 4 * A.brick_tile_ptr[brick] + lane; i < 4 * A.brick_tile_ptr[brick + 1]; i += 32)
+                am = max(am, A.tile_amax[i]);
             for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
             const float bnd = A.brick_cv[brick] * __uint_as_float(d1_bits) * __uint_as_float(am);
             int bexp = 0;
@@ -1549,7 +1558,7 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
 }
 
 life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate, int gate_mode,
-                  cudaStream_t s, const BatchGate& bg) {
+                  cudaStream_t s, const BatchGate& bg, bool r_is_dsc_out) {
     TcArgs A = make_args(ix);
     A.bg = bg;
     if (!A.status) {
@@ -1570,7 +1579,7 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     }
     const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
     LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (ix->tile.n_tiles > 0) {
+    if (ix->tile.n_tiles > 0 && !r_is_dsc_out) {
         wc_amax_kernel<<<(unsigned)std::min<int64_t>(ix->tile.n_tiles, (int64_t)ix->num_sms * 8), AMAX_THREADS, 0, s>>>(A);
         LIFE_CHECK_LAUNCH();
     }
