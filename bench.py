@@ -30,16 +30,18 @@ UNIT = "iter/s"
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
-# DRAM bytes (read + write) of one launch of each tensor-core kernel on the
+# DRAM bytes (read + write) of the launches of one timed tensor-core call on the
 # paper-scale workload, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, a one-pass metric set): the DSC launch with the fused
-# residual and the WC launch of an SBB iteration.  The figures hold only for the
-# kernel source that was captured; after any change to it the bench reports null.
+# dram__bytes_write.sum, a one-pass metric set): DSC with the fused residual =
+# brick weight gather + DSC kernel; WC through the public call = per-tile max|r|
+# pass + WC kernel.  The figures hold only for the kernel source that was
+# captured; after any change to it the bench reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "0719d15577f56870d355295333dced46c96292c1952bf5ed78f2254aa86d052a",
+    "sha256": "08a755fa4d1320f907e533730196e91fd10c14342b1b37794f36281cb480e340",
     "nnz": 79521683,
-    "bytes": {"dsc": 649105664 + 114455552, "wc": 656090624 + 5174784},
+    "bytes": {"dsc": (38385920 + 901376) + (649159680 + 110891520),
+              "wc": (134848768 + 68352) + (656482304 + 5522432)},
 }
 
 
@@ -169,6 +171,12 @@ class GpuPath:
     def run_steps(self, k):
         self.life.life_sbbnnls_solve(self.idx, self.D, self.b, self.w, k, self.st, self.ws)
 
+    def run_steps_each(self, k):
+        """The same iterations as k single-step calls, so that every kernel is its
+        own launch (a profiler does not see inside the solve's conditional graph)."""
+        for _ in range(k):
+            self.life.life_sbbnnls_step(self.idx, self.D, self.b, self.w, self.st, self.ws)
+
 
 def time_steps(path, steps, warmup):
     import torch
@@ -214,15 +222,23 @@ def spmv_bytes(path, kind, fused_b=False):
     return phi + sig + 4 * p.n_fasc + dbytes
 
 
-def measure_kernels(life, path):
+def kernel_calls(life, path):
+    """The two SpMV calls whose launches the roofline times: DSC with the fused
+    residual, and WC through the public call (on the tensor-core path that is
+    the per-tile max|r| pass and the WC kernel)."""
     import torch
     p = path.p
     r = path.b
     g = torch.empty(p.n_fasc, dtype=torch.float32, device="cuda")
     e = torch.empty(p.n_theta * p.n_voxels, dtype=torch.float32, device="cuda")
     w = torch.rand(p.n_fasc, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
-    t_dsc = time_kernel(lambda: life.life_dsc(path.idx, path.D, w, b=path.b, y=e))
-    t_wc = time_kernel(lambda: life.life_wc(path.idx, path.D, r, g=g))
+    return (lambda: life.life_dsc(path.idx, path.D, w, b=path.b, y=e)), (lambda: life.life_wc(path.idx, path.D, r, g=g))
+
+
+def measure_kernels(life, path):
+    dsc_call, wc_call = kernel_calls(life, path)
+    t_dsc = time_kernel(dsc_call)
+    t_wc = time_kernel(wc_call)
     b_dsc = spmv_bytes(path, "dsc", fused_b=True)
     b_wc = spmv_bytes(path, "wc")
     return dict(dsc_s=t_dsc, wc_s=t_wc, dsc_bytes=b_dsc, wc_bytes=b_wc)
@@ -409,16 +425,20 @@ def run_ours(args):
             if rank == 0:
                 print(f"# bf16 tensor-core path unavailable: {e}", file=sys.stderr)
     if args.profile:
-        # Profiling mode: only the SBB steps of each path run between
-        # cudaProfilerStart/Stop (for ncu --profile-from-start off).
+        # Profiling mode: between cudaProfilerStart/Stop (for ncu
+        # --profile-from-start off) run only the SBB steps of each path (one call
+        # per step), then one of each of the DSC and WC calls that the roofline times.
         for name, path in paths.items():
             if path is None:
                 continue
             path.reset()
             path.run_steps(args.warmup)
+            dsc_call, wc_call = kernel_calls(life, path)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
-            path.run_steps(args.steps)
+            path.run_steps_each(args.steps)
+            dsc_call()
+            wc_call()
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
         if dist:

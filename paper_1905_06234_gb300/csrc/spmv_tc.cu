@@ -602,6 +602,7 @@ struct TcArgs {
     int nt, na, np, kp, n_sub, n_bricks, max_fb;
     int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
     int wgroups;         // WC: scatter warps per TMEM lane quarter (4, or 2 when shared memory is short)
+    int rbufs;           // WC: R tile buffers (2 when shared memory allows: the loader runs a tile ahead)
     BatchGate bg;        // batched launch: bricks of problems that are not live are skipped, and DSC
                          // partial sums go to partial[(p * grid + cta) * DSC_EPI_WARPS + epilogue warp]
 };
@@ -795,6 +796,44 @@ __device__ __forceinline__ void dsc_flush_sq(const TcArgs& A, double& sq, int p,
     sq = 0.0;
 }
 
+// D (Nθ x Na, θ fastest) into shared memory as a BF16 K-major MMA operand,
+// zero-padded to np x kp: ATOM_ROWS (WC: rows = atoms, K = θ) or not (DSC: rows
+// = θ, K = atoms).  Each step moves four θ of one atom with one 16-byte load, and
+// the loop is unrolled so that several loads are in flight.
+template <bool ATOM_ROWS>
+__device__ __forceinline__ void stage_d(const TcArgs& A, unsigned char* dst, uint32_t sbo, int tid, int nthr) {
+    const int q4 = A.np >> 2, n = A.kp * q4;
+    const bool vec = (A.nt & 3) == 0 && (reinterpret_cast<uintptr_t>(A.D) & 15) == 0;
+#pragma unroll 4
+    for (int g = tid; g < n; g += nthr) {
+        const int a = g / q4, t0 = 4 * (g - a * q4);
+        float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (a < A.na && t0 < A.nt) {
+            const float* src = A.D + (int64_t)A.nt * a + t0;
+            if (vec) {
+                d = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+                d.x = __ldg(src);
+                if (t0 + 1 < A.nt) d.y = __ldg(src + 1);
+                if (t0 + 2 < A.nt) d.z = __ldg(src + 2);
+                if (t0 + 3 < A.nt) d.w = __ldg(src + 3);
+            }
+        }
+        if (ATOM_ROWS) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(d.x, d.y), hi = __floats2bfloat162_rn(d.z, d.w);
+            uint2 v;
+            v.x = *reinterpret_cast<const uint32_t*>(&lo);
+            v.y = *reinterpret_cast<const uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(dst + kmajor_off(a, t0, sbo)) = v;  // K = θ: 4 consecutive bf16
+        } else {
+            *reinterpret_cast<__nv_bfloat16*>(dst + kmajor_off(t0, a, sbo)) = __float2bfloat16_rn(d.x);
+            *reinterpret_cast<__nv_bfloat16*>(dst + kmajor_off(t0 + 1, a, sbo)) = __float2bfloat16_rn(d.y);
+            *reinterpret_cast<__nv_bfloat16*>(dst + kmajor_off(t0 + 2, a, sbo)) = __float2bfloat16_rn(d.z);
+            *reinterpret_cast<__nv_bfloat16*>(dst + kmajor_off(t0 + 3, a, sbo)) = __float2bfloat16_rn(d.w);
+        }
+    }
+}
+
 __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
@@ -816,11 +855,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     const uint32_t SBO_D = (uint32_t)(A.kp / 8) * 128u;
 
     // D as the B operand: rows θ (N), K = atoms; bf16, zero-padded.
-    for (int i = tid; i < A.np * A.kp; i += blockDim.x) {
-        const int t = i % A.np, a = i / A.np;
-        const float d = (t < A.nt && a < A.na) ? A.D[t + (int64_t)A.nt * a] : 0.0f;
-        *reinterpret_cast<__nv_bfloat16*>(Ds + kmajor_off(t, a, SBO_D)) = __float2bfloat16_rn(d);
-    }
+    stage_d<false>(A, Ds, SBO_D, tid, blockDim.x);
     if (tid == 0) {
         for (int s = 0; s < DSTAGE; ++s) {
             mbar_init(&full_bar[s], DSC_PROD_WARPS);
@@ -1121,12 +1156,12 @@ constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
 constexpr int ZW = 33;                                // row stride (floats) of a warp's Z tile
 constexpr uint32_t ZW_BYTES = 32 * ZW * 4;
 
-__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups) {
+__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups, int rbufs = 1) {
     uint32_t d = (uint32_t)kp * np * 2;
     d = (d + 1023) / 1024 * 1024;
     uint32_t r = (uint32_t)TILE_V * np * 2;
     r = (r + 1023) / 1024 * 1024;
-    return d + r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
+    return d + (uint32_t)rbufs * r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
 // FIXED: the table holds 32-bit integers in units of 1/sc (sc a power of two chosen
@@ -1220,7 +1255,7 @@ __global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
 
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t r_full, r_empty, z_full, z_empty, fin_bar;
+    __shared__ uint64_t r_full[2], r_empty[2], z_full, z_empty, fin_bar;
     __shared__ uint32_t tmem_base, d1_bits;
     __shared__ int abort_flag, never;
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
@@ -1231,20 +1266,18 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     const uint32_t r_bytes = align_up((uint32_t)TILE_V * A.np * 2, 1024);
     const int wg = A.wgroups;
     unsigned char* Dw = smem;
-    unsigned char* Rs = smem + d_bytes;
-    float* Zc = reinterpret_cast<float*>(Rs + r_bytes);
+    unsigned char* Rs = smem + d_bytes;  // A.rbufs tiles of r_bytes
+    float* Zc = reinterpret_cast<float*>(Rs + A.rbufs * r_bytes);
     float* gl = Zc + 4 * wg * (ZW_BYTES / 4);
     const uint32_t SBO_K = (uint32_t)(A.np / 8) * 128u;  // 8-row groups of both operands (K = θ)
 
     // D as the B operand: rows = atoms (N), K = θ; bf16, zero-padded.
-    for (int i = tid; i < A.kp * A.np; i += blockDim.x) {
-        const int t = i % A.np, a = i / A.np;
-        const float d = (t < A.nt && a < A.na) ? A.D[t + (int64_t)A.nt * a] : 0.0f;
-        *reinterpret_cast<__nv_bfloat16*>(Dw + kmajor_off(a, t, SBO_K)) = __float2bfloat16_rn(d);
-    }
+    stage_d<true>(A, Dw, SBO_K, tid, blockDim.x);
     if (tid == 0) {
-        mbar_init(&r_full, WC_LOAD_WARPS);
-        mbar_init(&r_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&r_full[b], WC_LOAD_WARPS);
+            mbar_init(&r_empty[b], 1);
+        }
         mbar_init(&z_full, 1);
         mbar_init(&z_empty, WC_SCAT_WARPS);
         mbar_init(&fin_bar, 1);
@@ -1308,12 +1341,20 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             named_bar_sync(2, WC_SCAT_THREADS);
             const int t0 = A.brick_tile_ptr[brick], t1 = A.brick_tile_ptr[brick + 1];
             // this warp's segments in order: (t, s) for t in the brick, s = h, h + wg, ...;
-            // the first slot of the next segment is loaded while the current one is processed
+            // a warp step covers two 256-entry blocks (lane i: entries 8i.. of each),
+            // and the step after it (or the next segment's first) is loaded while the
+            // current one is processed
             const EntrySlot zero{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-            int beg = active ? wseg(A, t0, q, h) : 0, end = active ? wseg(A, t0, q, h + 1) : 0;
+            constexpr int BLK = 32 * SLOT;
+            // segment bounds of this tile and the next, lane i holding wseg(t, q, i) for i <= n_sub
+            int bnd_cur = (active && lane <= A.n_sub) ? wseg(A, t0, q, lane) : 0;
+            int bnd_nxt = (active && lane <= A.n_sub && t0 + 1 < t1) ? wseg(A, t0 + 1, q, lane) : 0;
+            int beg = __shfl_sync(0xffffffffu, bnd_cur, h), end = __shfl_sync(0xffffffffu, bnd_cur, h + 1);
+            if (!active) beg = end = 0;
             int base = (beg & ~7) + lane * SLOT;
-            EntrySlot cur = zero;
-            if (active && base < end) wc_load_slot(A, base, cur);
+            EntrySlot cur0 = zero, cur1 = zero;
+            if (active && base < end) wc_load_slot(A, base, cur0);
+            if (active && base + BLK < end) wc_load_slot(A, base + BLK, cur1);
             for (int t = t0; t < t1 && !dead; ++t, ++tcount) {
                 if (!warp_wait(&z_full, tcount & 1u, &abort_flag)) {
                     abort_flag = 1;
@@ -1323,49 +1364,62 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                 tc_fence_after();
                 if (active) {
                     for (int s = h; s < A.n_sub; s += wg) {
-                        uint32_t rr[32];
-                        tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * s), rr);
-                        tmem_ld_wait();
-                        float* zrow = Zw + lane * ZW;
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
-                        __syncwarp();
                         int ns = s + wg, nt = t;
                         if (ns >= A.n_sub) {
                             ns = h;
                             ++nt;
                         }
                         const bool nvalid = nt < t1;
-                        const int nbeg = nvalid ? wseg(A, nt, q, ns) : 0, nend = nvalid ? wseg(A, nt, q, ns + 1) : 0;
+                        const int nb_src = nt == t ? bnd_cur : bnd_nxt;
+                        const int nbeg0 = __shfl_sync(0xffffffffu, nb_src, ns), nend0 = __shfl_sync(0xffffffffu, nb_src, ns + 1);
+                        const int nbeg = nvalid ? nbeg0 : 0, nend = nvalid ? nend0 : 0;
                         const int nbase = (nbeg & ~7) + lane * SLOT;
-                        EntrySlot nxt = zero;
-                        bool pf = false;
-                        while (__shfl_sync(0xffffffffu, base, 0) < end) {
-                            const int b2 = base + 32 * SLOT;
-                            const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;
-                            if (more) {
-                                nxt = zero;
-                                if (b2 < end) wc_load_slot(A, b2, nxt);
-                            } else if (nbase < nend) {
-                                wc_load_slot(A, nbase, nxt);
-                                pf = true;
+                        EntrySlot nxt0 = zero, nxt1 = zero;
+                        if (beg < end) {  // an empty segment needs neither Z nor a pass
+                            uint32_t rr[32];
+                            tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * s), rr);
+                            tmem_ld_wait();
+                            float* zrow = Zw + lane * ZW;
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                            __syncwarp();
+                            for (;;) {
+                                const int b2 = base + 2 * BLK;
+                                const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;
+                                if (more) {
+                                    if (b2 < end) wc_load_slot(A, b2, nxt0);
+                                    if (b2 + BLK < end) wc_load_slot(A, b2 + BLK, nxt1);
+                                } else {
+                                    if (nbase < nend) wc_load_slot(A, nbase, nxt0);
+                                    if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
+                                }
+                                if (fixed) {
+                                    wc_slot<true>(cur0, base, beg, end, Zw, gl, gl_s, sc);
+                                    wc_slot<true>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                } else {
+                                    wc_slot<false>(cur0, base, beg, end, Zw, gl, gl_s, sc);
+                                    wc_slot<false>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                }
+                                if (!more) break;
+                                cur0 = nxt0;
+                                cur1 = nxt1;
+                                nxt0 = zero;
+                                nxt1 = zero;
+                                base = b2;
                             }
-                            if (fixed) wc_slot<true>(cur, base, beg, end, Zw, gl, gl_s, sc);
-                            else wc_slot<false>(cur, base, beg, end, Zw, gl, gl_s, sc);
-                            if (!more) break;
-                            cur = nxt;
-                            base = b2;
+                            __syncwarp();
+                        } else {
+                            if (nbase < nend) wc_load_slot(A, nbase, nxt0);
+                            if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
                         }
-                        if (!pf) {
-                            nxt = zero;
-                            if (nbase < nend) wc_load_slot(A, nbase, nxt);
-                        }
-                        cur = nxt;
+                        cur0 = nxt0;
+                        cur1 = nxt1;
                         base = nbase;
                         beg = nbeg;
                         end = nend;
-                        __syncwarp();
                     }
+                    bnd_cur = bnd_nxt;
+                    bnd_nxt = (lane <= A.n_sub && t + 2 < t1) ? wseg(A, t + 2, q, lane) : 0;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -1384,8 +1438,13 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         for (int r = 0; !stop; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
+            int r_next = r + 1;
+            const int next_brick = live_brick(A, G, cta, r_next);
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
-                if (!warp_wait(&r_empty, (tcount & 1u) ^ 1u, &abort_flag)) {
+                // R buffer rb, used for the k-th time (tiles go round the buffers)
+                const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
+                unsigned char* Rb = Rs + rb * r_bytes;
+                if (!warp_wait(&r_empty[rb], (rk & 1u) ^ 1u, &abort_flag)) {
                     abort_flag = 1;
                     stop = true;
                     break;
@@ -1430,20 +1489,40 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                         pk.y = *reinterpret_cast<uint32_t*>(&p1);
                         pk.z = *reinterpret_cast<uint32_t*>(&p2);
                         pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                        *reinterpret_cast<uint4*>(Rs + kmajor_off(row, 8 * g8, SBO_K)) = pk;
+                        *reinterpret_cast<uint4*>(Rb + kmajor_off(row, 8 * g8, SBO_K)) = pk;
                     }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&r_full);
+                if (lane == 0) mbar_arrive(&r_full[rb]);
                 ++tcount;
+                // pull the voxel rows of r of the tile A.rbufs ahead into L2 (the
+                // loader runs A.rbufs - 1 tiles ahead of the tensor cores), so that
+                // loading it later is not a chain of DRAM round trips
+                int tn = t + A.rbufs;
+                if (tn >= A.brick_tile_ptr[brick + 1]) {
+                    tn -= A.brick_tile_ptr[brick + 1];
+                    tn = (next_brick >= 0 && A.brick_tile_ptr[next_brick] + tn < A.brick_tile_ptr[next_brick + 1])
+                             ? A.brick_tile_ptr[next_brick] + tn : -1;
+                }
+                if (tn >= 0) {
+                    const int32_t* tvn = A.tile_vox + (int64_t)tn * TILE_V;
+                    for (int row = lt; row < TILE_V; row += WC_LOAD_THREADS) {
+                        const int v = __ldg(tvn + row);
+                        if (v < 0) continue;
+                        const char* a = reinterpret_cast<const char*>(A.x + (int64_t)A.nt * v);
+                        const char* e = a + 4 * A.nt - 1;
+                        for (const char* c = a; c < e; c += 128) prefetch_l2(c);
+                        prefetch_l2(e);
+                    }
+                }
             }
         }
     } else if (lane == 0) {
         // ---------------- MMA issuer: Zᵀ[128 x kp] = R[128 x np] · Dᵀ (kp split in N <= 256 pieces)
         const int nh = A.kp <= 256 ? A.kp : A.kp / 2;
         const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)nh);
-        const uint32_t sR = smem_u32(Rs), sD = smem_u32(Dw);
+        const uint32_t sR0 = smem_u32(Rs), sD = smem_u32(Dw);
         uint32_t tcount = 0;
         bool stop = false;
         for (int r = 0; !stop; ++r) {
@@ -1451,7 +1530,9 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             if (brick < 0) break;
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
                 const uint32_t ph = tcount & 1u;
-                if (!mbar_wait(&r_full, ph, &abort_flag, WAIT_LIMIT) ||
+                const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
+                const uint32_t sR = sR0 + rb * r_bytes;
+                if (!mbar_wait(&r_full[rb], rk & 1u, &abort_flag, WAIT_LIMIT) ||
                     !mbar_wait(&z_empty, ph ^ 1u, &abort_flag, WAIT_LIMIT)) {
                     abort_flag = 1;
                     stop = true;
@@ -1465,7 +1546,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                         mma_bf16(tb + (uint32_t)n0, ad, bd, idesc, kk != 0 ? 1u : 0u);
                     }
                 }
-                mma_commit(&r_empty);
+                mma_commit(&r_empty[rb]);
                 mma_commit(&z_full);
                 ++tcount;
             }
@@ -1493,6 +1574,14 @@ int wc_effective_groups(const life_index_s* ix) {
     int wg = ix->wc_groups > 0 ? ix->wc_groups : 4;
     while (wg >= 1 && wc_smem_bytes(L.np, L.kp, L.max_fb, wg) + 256 > (uint32_t)optin) wg /= 2;
     return wg;
+}
+
+// R tile buffers of the WC kernel with wg scatter groups: two when they fit.
+static int wc_r_buffers(const life_index_s* ix, int wg) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device) != cudaSuccess) return 1;
+    const TileLayout& L = ix->tile;
+    return wc_smem_bytes(L.np, L.kp, L.max_fb, wg, 2) + 256 <= (uint32_t)optin ? 2 : 1;
 }
 
 static TcArgs make_args(life_index_s* ix) {
@@ -1577,7 +1666,8 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
                   wc_smem_bytes(A.np, A.kp, A.max_fb, 1));
         return LIFE_ENOTSUP;
     }
-    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups);
+    A.rbufs = wc_r_buffers(ix, A.wgroups);
+    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups, A.rbufs);
     LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ix->tile.n_tiles > 0 && !r_is_dsc_out) {
         wc_amax_kernel<<<(unsigned)std::min<int64_t>(ix->tile.n_tiles, (int64_t)ix->num_sms * 8), AMAX_THREADS, 0, s>>>(A);

@@ -24,6 +24,11 @@ __device__ __forceinline__ void red_add_shared_f32(uint32_t addr, float x) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(x) : "memory");
 }
 
+// Hint: bring the L2 line holding p (device global memory) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 // Adds x to the FP32 word at p, which points into device global memory.
 __device__ __forceinline__ void red_add_global_f32(float* p, float x) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(x) : "memory");
