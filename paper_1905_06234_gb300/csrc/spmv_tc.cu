@@ -686,18 +686,19 @@ __device__ __forceinline__ bool next_chunk(const TcArgs& A, int G, int cta, int 
 // With inv != 0 the table holds int32 values in units of inv.
 __device__ __forceinline__ void flush_table(float* dst, const float* tab, const int32_t* __restrict__ idx, int n,
                                             int tid, int nthr, float inv = 0.0f) {
-    for (int b0 = 0; b0 < n; b0 += 8 * nthr) {
-        int id[8];
-        float v[8];
+    constexpr int U = 16;  // index loads in flight per thread
+    for (int b0 = 0; b0 < n; b0 += U * nthr) {
+        int id[U];
+        float v[U];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < U; ++e) {
             const int i = b0 + e * nthr + tid;
             v[e] = i < n ? tab[i] : 0.0f;
             if (inv != 0.0f) v[e] = (float)__float_as_int(v[e]) * inv;
             id[e] = (i < n && v[e] != 0.0f) ? __ldg(idx + i) : -1;
         }
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
+        for (int e = 0; e < U; ++e)
             if (id[e] >= 0) red_add_global_f32(dst + id[e], v[e]);
     }
 }
@@ -1336,6 +1337,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             (void)frexpf(bnd, &bexp);
             const bool fixed = bnd <= 3.0e38f && bnd >= 1.0e-27f;
             const float sc = fixed ? ldexpf(1.0f, 29 - bexp) : 0.0f, inv = fixed ? ldexpf(1.0f, bexp - 29) : 0.0f;
+            // the table's global fascicle ids, read by the flush at the brick's end
+            for (int i = 32 * tid; i < nfb; i += 32 * WC_SCAT_THREADS) prefetch_l2(A.brick_fasc + fb0 + i);
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
             for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
             named_bar_sync(2, WC_SCAT_THREADS);
