@@ -38,10 +38,10 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # captured; after any change to it the bench reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "08a755fa4d1320f907e533730196e91fd10c14342b1b37794f36281cb480e340",
+    "sha256": "af807377ad62f0ce4edce0c02462c1e4a1716b5c7b7ae5cce4fee061b51c7d02",
     "nnz": 79521683,
-    "bytes": {"dsc": (38385920 + 901376) + (649159680 + 110891520),
-              "wc": (134848768 + 68352) + (656482304 + 5522432)},
+    "bytes": {"dsc": (38386176 + 48896) + (649159680 + 110672640),
+              "wc": (134852608 + 406272) + (687121152 + 5548288)},
 }
 
 
