@@ -1155,6 +1155,10 @@ constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
 constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
 constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
 constexpr int ZW = 33;                                // row stride (floats) of a warp's Z tile
+// Z goes through tensor memory in 128-atom chunks: a ring of ZSLOTS slots of 128
+// columns (all 512), so the tensor cores can fill the next chunks while the
+// scatter warps still work on earlier ones
+constexpr int ZSLOTS = 4;
 constexpr uint32_t ZW_BYTES = 32 * ZW * 4;
 
 __host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups, int rbufs = 1) {
@@ -1256,7 +1260,7 @@ __global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
 
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t r_full[2], r_empty[2], z_full, z_empty, fin_bar;
+    __shared__ uint64_t r_full[2], r_empty[2], z_full[ZSLOTS], z_empty[ZSLOTS], fin_bar;
     __shared__ uint32_t tmem_base, d1_bits;
     __shared__ int abort_flag, never;
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
@@ -1279,8 +1283,10 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             mbar_init(&r_full[b], WC_LOAD_WARPS);
             mbar_init(&r_empty[b], 1);
         }
-        mbar_init(&z_full, 1);
-        mbar_init(&z_empty, WC_SCAT_WARPS);
+        for (int z = 0; z < ZSLOTS; ++z) {
+            mbar_init(&z_full[z], 1);
+            mbar_init(&z_empty[z], WC_SCAT_WARPS);
+        }
         mbar_init(&fin_bar, 1);
         abort_flag = 0;
         never = 0;
@@ -1317,7 +1323,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         const bool active = h < wg;               // warps beyond wgroups groups only keep step
         float* Zw = Zc + (active ? (h * 4 + q) : 0) * (ZW_BYTES / 4);
         const uint32_t gl_s = smem_u32(gl);
-        uint32_t tcount = 0;
+        const int kc = A.kp / 128;  // 128-atom chunks per tile
+        uint32_t kcount = 0;        // chunks handed over so far (ring position)
         bool dead = false;
         for (int r = 0;; ++r) {
             const int brick = live_brick(A, G, cta, r);
@@ -1358,75 +1365,81 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             EntrySlot cur0 = zero, cur1 = zero;
             if (active && base < end) wc_load_slot(A, base, cur0);
             if (active && base + BLK < end) wc_load_slot(A, base + BLK, cur1);
-            for (int t = t0; t < t1 && !dead; ++t, ++tcount) {
-                if (!warp_wait(&z_full, tcount & 1u, &abort_flag)) {
-                    abort_flag = 1;
-                    dead = true;
-                    break;
-                }
-                tc_fence_after();
-                if (active) {
-                    for (int s = h; s < A.n_sub; s += wg) {
-                        int ns = s + wg, nt = t;
-                        if (ns >= A.n_sub) {
-                            ns = h;
-                            ++nt;
-                        }
-                        const bool nvalid = nt < t1;
-                        const int nb_src = nt == t ? bnd_cur : bnd_nxt;
-                        const int nbeg0 = __shfl_sync(0xffffffffu, nb_src, ns), nend0 = __shfl_sync(0xffffffffu, nb_src, ns + 1);
-                        const int nbeg = nvalid ? nbeg0 : 0, nend = nvalid ? nend0 : 0;
-                        const int nbase = (nbeg & ~7) + lane * SLOT;
-                        EntrySlot nxt0 = zero, nxt1 = zero;
-                        if (beg < end) {  // an empty segment needs neither Z nor a pass
-                            uint32_t rr[32];
-                            tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * s), rr);
-                            tmem_ld_wait();
-                            float* zrow = Zw + lane * ZW;
-#pragma unroll
-                            for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
-                            __syncwarp();
-                            for (;;) {
-                                const int b2 = base + 2 * BLK;
-                                const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;
-                                if (more) {
-                                    if (b2 < end) wc_load_slot(A, b2, nxt0);
-                                    if (b2 + BLK < end) wc_load_slot(A, b2 + BLK, nxt1);
-                                } else {
-                                    if (nbase < nend) wc_load_slot(A, nbase, nxt0);
-                                    if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
-                                }
-                                if (fixed) {
-                                    wc_slot<true>(cur0, base, beg, end, Zw, gl, gl_s, sc);
-                                    wc_slot<true>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
-                                } else {
-                                    wc_slot<false>(cur0, base, beg, end, Zw, gl, gl_s, sc);
-                                    wc_slot<false>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
-                                }
-                                if (!more) break;
-                                cur0 = nxt0;
-                                cur1 = nxt1;
-                                nxt0 = zero;
-                                nxt1 = zero;
-                                base = b2;
-                            }
-                            __syncwarp();
-                        } else {
-                            if (nbase < nend) wc_load_slot(A, nbase, nxt0);
-                            if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
-                        }
-                        cur0 = nxt0;
-                        cur1 = nxt1;
-                        base = nbase;
-                        beg = nbeg;
-                        end = nend;
+            for (int t = t0; t < t1 && !dead; ++t) {
+                for (int j = 0; j < kc && !dead; ++j, ++kcount) {
+                    // chunk j (atoms 128j ..) of tile t sits in slot zs of the ring
+                    const uint32_t zs = kcount % ZSLOTS, zu = (kcount / ZSLOTS) & 1u;
+                    if (!warp_wait(&z_full[zs], zu, &abort_flag)) {
+                        abort_flag = 1;
+                        dead = true;
+                        break;
                     }
+                    tc_fence_after();
+                    if (active) {
+                        for (int s = 4 * j + h; s < 4 * j + 4; s += wg) {
+                            int ns = s + wg, nt = t;
+                            if (ns >= A.n_sub) {
+                                ns = h;
+                                ++nt;
+                            }
+                            const bool nvalid = nt < t1;
+                            const int nb_src = nt == t ? bnd_cur : bnd_nxt;
+                            const int nbeg0 = __shfl_sync(0xffffffffu, nb_src, ns), nend0 = __shfl_sync(0xffffffffu, nb_src, ns + 1);
+                            const int nbeg = nvalid ? nbeg0 : 0, nend = nvalid ? nend0 : 0;
+                            const int nbase = (nbeg & ~7) + lane * SLOT;
+                            EntrySlot nxt0 = zero, nxt1 = zero;
+                            if (beg < end) {  // an empty segment needs neither Z nor a pass
+                                uint32_t rr[32];
+                                tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + zs * 128u + (uint32_t)(32 * (s - 4 * j)), rr);
+                                tmem_ld_wait();
+                                float* zrow = Zw + lane * ZW;
+#pragma unroll
+                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                                __syncwarp();
+                                for (;;) {
+                                    const int b2 = base + 2 * BLK;
+                                    const bool more = __shfl_sync(0xffffffffu, b2, 0) < end;
+                                    if (more) {
+                                        if (b2 < end) wc_load_slot(A, b2, nxt0);
+                                        if (b2 + BLK < end) wc_load_slot(A, b2 + BLK, nxt1);
+                                    } else {
+                                        if (nbase < nend) wc_load_slot(A, nbase, nxt0);
+                                        if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
+                                    }
+                                    if (fixed) {
+                                        wc_slot<true>(cur0, base, beg, end, Zw, gl, gl_s, sc);
+                                        wc_slot<true>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                    } else {
+                                        wc_slot<false>(cur0, base, beg, end, Zw, gl, gl_s, sc);
+                                        wc_slot<false>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                    }
+                                    if (!more) break;
+                                    cur0 = nxt0;
+                                    cur1 = nxt1;
+                                    nxt0 = zero;
+                                    nxt1 = zero;
+                                    base = b2;
+                                }
+                                __syncwarp();
+                            } else {
+                                if (nbase < nend) wc_load_slot(A, nbase, nxt0);
+                                if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
+                            }
+                            cur0 = nxt0;
+                            cur1 = nxt1;
+                            base = nbase;
+                            beg = nbeg;
+                            end = nend;
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&z_empty[zs]);  // this warp is done with the slot
+                }
+                if (active) {
                     bnd_cur = bnd_nxt;
                     bnd_nxt = (lane <= A.n_sub && t + 2 < t1) ? wseg(A, t + 2, q, lane) : 0;
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&z_empty);  // this warp is done with the tile's TMEM
             }
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
             flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS, inv);
@@ -1522,35 +1535,41 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             }
         }
     } else if (lane == 0) {
-        // ---------------- MMA issuer: Zᵀ[128 x kp] = R[128 x np] · Dᵀ (kp split in N <= 256 pieces)
-        const int nh = A.kp <= 256 ? A.kp : A.kp / 2;
-        const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)nh);
+        // ---------------- MMA issuer: Zᵀ[128 x kp] = R[128 x np] · Dᵀ, one 128-atom chunk
+        // (N = 128) at a time into the next slot of the tensor-memory ring
+        const uint32_t idesc = idesc_bf16_f32(128, 128u);
         const uint32_t sR0 = smem_u32(Rs), sD = smem_u32(Dw);
-        uint32_t tcount = 0;
+        const int kc = A.kp / 128;
+        uint32_t tcount = 0, kcount = 0;
         bool stop = false;
         for (int r = 0; !stop; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
-            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
-                const uint32_t ph = tcount & 1u;
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1] && !stop; ++t) {
                 const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
                 const uint32_t sR = sR0 + rb * r_bytes;
-                if (!mbar_wait(&r_full[rb], rk & 1u, &abort_flag, WAIT_LIMIT) ||
-                    !mbar_wait(&z_empty, ph ^ 1u, &abort_flag, WAIT_LIMIT)) {
+                if (!mbar_wait(&r_full[rb], rk & 1u, &abort_flag, WAIT_LIMIT)) {
                     abort_flag = 1;
                     stop = true;
                     break;
                 }
-                tc_fence_after();
-                for (int n0 = 0; n0 < A.kp; n0 += nh) {
+                for (int j = 0; j < kc; ++j, ++kcount) {
+                    const uint32_t zs = kcount % ZSLOTS, zu = (kcount / ZSLOTS) & 1u;
+                    if (!mbar_wait(&z_empty[zs], zu ^ 1u, &abort_flag, WAIT_LIMIT)) {  // the slot's last chunk is read
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
                     for (int kk = 0; kk < A.np / 16; ++kk) {
                         const uint64_t ad = smem_desc(sR + kk * 256u, 128u, SBO_K);
-                        const uint64_t bd = smem_desc(sD + (uint32_t)(n0 / 8) * SBO_K + kk * 256u, 128u, SBO_K);
-                        mma_bf16(tb + (uint32_t)n0, ad, bd, idesc, kk != 0 ? 1u : 0u);
+                        const uint64_t bd = smem_desc(sD + (uint32_t)(16 * j) * SBO_K + kk * 256u, 128u, SBO_K);
+                        mma_bf16(tb + zs * 128u, ad, bd, idesc, kk != 0 ? 1u : 0u);
                     }
+                    mma_commit(&z_full[zs]);
                 }
+                if (stop) break;
                 mma_commit(&r_empty[rb]);
-                mma_commit(&z_full);
                 ++tcount;
             }
         }
