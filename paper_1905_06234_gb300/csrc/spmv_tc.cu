@@ -1149,7 +1149,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
 // is ordered by (tile, row quarter, atom, row, fascicle) for exactly this).
 
 constexpr int WC_SCAT_WARPS = 16;
-constexpr int WC_LOAD_WARPS = 3;     // 20 warps in all (see DSC_PROD_WARPS)
+constexpr int WC_LOAD_WARPS = 3;     // 20 warps in all: at 96 registers an SM sub-partition (16K registers) holds 5
 constexpr int WC_MMA_WARP = WC_SCAT_WARPS + WC_LOAD_WARPS;
 constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
 constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
