@@ -271,10 +271,16 @@ def e2e_steps(life, path, steps, warmup):
 
 
 def launches_per_step(path):
-    # DSC + WC + project + scalars + DSC + WC + sumsq + scalars + update, and on the
-    # tensor-core path the brick weight gather before each of the two DSCs and the
-    # per-brick max |r| pass before each of the two WCs
-    return 13 if path.info["algo"] == 2 else 9
+    # DSC + WC + project + scalars + DSC + WC + sumsq + scalars + update + the
+    # solve loop's condition kernel, and on the tensor-core path the brick weight
+    # gather before each of the two DSCs (the WCs take the per-tile max |r| from
+    # the DSC before them, so the step launches no separate max pass)
+    return 12 if path.info["algo"] == 2 else 10
+
+
+def launches_per_solve(path, steps):
+    """Kernels of one timed solve: the steps plus the loop-counter initialisation."""
+    return launches_per_step(path) * steps + 1
 
 
 def max_over_ranks(value, dist, device):
@@ -506,7 +512,7 @@ def run_ours(args):
                          "sample": "one FP64 SBB iteration on the voxels 0..%d sub-problem (%d of %d raw entries), "
                                    "scaled by the entry fraction" % (cpu["nv_sample"], cpu["nnz_sample"], p.n_raw)},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step(path) * (args.steps) * world,
+        "gpu_launches": launches_per_solve(path, args.steps) * world,
         "clocks": best["clocks"],
         "final_state": {"it": st["it"], "obj": st["obj"], "alpha": st["alpha"]},
         "tile_layout": {k: path.info[k] for k in ("brick_edge", "wc_groups", "tuned")},
