@@ -113,7 +113,9 @@ LIFE_API life_status life_index_get_info(life_index idx, life_index_info* out);
  * Writes the merged Phi in one of the paper's restructured orders (Sec. 4.1.2):
  * LIFE_LAYOUT_VOXEL sorted by (v, a, f), LIFE_LAYOUT_FIBER by (f, v, a),
  * LIFE_LAYOUT_ATOM by (a, v, f).  Device outputs of info.nnz entries each.
- * Stored BF16 values are widened back to float32.  May allocate temporary device
+ * Values are the merged float32 values (each duplicate sum rounded once), also
+ * for a BF16 index: the BF16 rounding of the streamed layouts is visible through
+ * life_index_export_voxel_streams and life_index_export_tiles.  May allocate temporary device
  * memory; synchronizes `stream`.
  */
 LIFE_API life_status life_index_export(life_index idx, int32_t layout, int32_t* atom, int32_t* voxel,

@@ -253,8 +253,8 @@ __global__ void graddD_chunk_kernel(const int32_t* __restrict__ chunk_beg, int n
         for (int q = 0; q < NTW; ++q) acc[q] = 0.0f;
         const int beg = chunk_beg[c], end = chunk_beg[c + 1];
         for (int k = beg; k < end; ++k) {
+            // no skip on s == 0: a NaN or inf in gy must reach dL/dD as in the oracle
             const float s = val[k] * w[fasc[k]];
-            if (s == 0.0f) continue;
             const float* e = gy + (int64_t)nt * voxel[k];
 #pragma unroll
             for (int q = 0; q < NTW; ++q) {

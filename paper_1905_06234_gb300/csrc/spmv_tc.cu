@@ -983,7 +983,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 cur = nxt;  // an empty slot when this lane has none in the next chunk
             }
             // no bulk table copy may still be writing shared memory when the CTA exits
-            if (tid == 0 && tab_n > 0) mbar_wait(&tab_bar, (tab_n - 1) & 1u, &never, WAIT_LIMIT);
+            if (tid == 0 && tab_n > 0 && !mbar_wait(&tab_bar, (tab_n - 1) & 1u, &never, WAIT_LIMIT)) abort_flag = 1;
         }
     } else if (warp < DSC_MMA_WARP) {
         // ---------------- epilogue: TMEM -> y (− b), Σ y² (FP32 per row and tile, FP64 across)
@@ -1122,18 +1122,21 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             }
         }
         mma_commit(&fin_bar);
-        mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT);
+        // a wait that gives up marks the call failed (the host sees LIFE_ETIMEOUT)
+        if (!mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT)) abort_flag = 1;
         // no bulk copy may still be writing shared memory when the CTA exits
-        for (int z = 0; z < DSTAGE; ++z) mbar_wait(&zero_bar[z], (zlast >> z) & 1u, &never, WAIT_LIMIT);
+        for (int z = 0; z < DSTAGE; ++z)
+            if (!mbar_wait(&zero_bar[z], (zlast >> z) & 1u, &never, WAIT_LIMIT)) abort_flag = 1;
     }
-    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     tc_fence_before();
     __syncthreads();
+    // every role's abort decision is visible after the barrier
+    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     if (warp == DSC_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tb, 256);
     }
-    if (tid == 0 && A.partial && !A.bg.live) {
+    if (tid == 0 && A.partial && !A.bg.live && !abort_flag) {
         double tot = 0.0;
         for (int e = 0; e < DSC_EPI_WARPS; ++e) tot += red[e];
         A.partial[blockIdx.x] = tot;
@@ -1574,11 +1577,11 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             }
         }
         mma_commit(&fin_bar);
-        mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT);
+        if (!mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT)) abort_flag = 1;
     }
-    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     tc_fence_before();
     __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     if (warp == WC_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tb, 512);
