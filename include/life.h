@@ -271,6 +271,43 @@ LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const fl
                                int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
                                void* workspace, void* stream);
 
+/* --------------------------------------------------- connectome evaluation */
+
+/*
+ * The pruned connectome.  LiFE keeps the fascicles whose fitted weight is
+ * positive and discards the rest (Sec. 1, Sec. 2.1: the candidate connectome is
+ * pruned to the subset of fascicles that predicts the signal).
+ *  w          float32 [Nf] weights (normally an SBB-NNLS solution)
+ *  threshold  a fascicle is kept when w[f] > threshold (0 = positive weight);
+ *             a NaN weight is never kept
+ *  keep       uint8 [Nf] output or NULL: 1 for kept fascicles, else 0
+ *  kept       int32 [Nf] output or NULL: the kept fascicle ids in increasing order
+ *             (the first *n_kept entries are written)
+ *  n_kept     int64 [1] device output or NULL: the number of kept fascicles
+ *  w_pruned   float32 [Nf] output or NULL: w on kept fascicles, 0 elsewhere (the
+ *             weights of the pruned model, for a DSC that predicts with it)
+ * Deterministic (an ordered stream compaction).  May allocate temporary device
+ * memory on `stream`.  Errors: LIFE_EINVAL for n_fasc < 0, a NULL w with
+ * n_fasc > 0, or no output at all.
+ */
+LIFE_API life_status life_prune(int32_t n_fasc, const float* w, float threshold, uint8_t* keep, int32_t* kept,
+                                int64_t* n_kept, float* w_pruned, void* stream);
+
+/*
+ * Per-voxel prediction error of the model y ≈ M w (Eq. 1), the measure by which
+ * LiFE judges how well a connectome explains the measured diffusion signal
+ * (Sec. 2.1): given the residual e = M w − b (life_dsc with b),
+ *   rmse[v] = sqrt( Σ_θ e[θ,v]² / Nθ ),
+ * each sum in FP64, rounded once to float32.
+ *  e      float32 [Nθ·Nv] residual, column-major [θ + Nθ·v]
+ *  rmse   float32 [Nv] output or NULL
+ *  sumsq  double [1] device output or NULL: Σ over all (θ,v) of e² in FP64
+ * May allocate temporary device memory on `stream`.
+ * Errors: LIFE_EINVAL for n_theta < 1, n_voxels < 0, a NULL e, or no output.
+ */
+LIFE_API life_status life_voxel_rmse(int32_t n_theta, int32_t n_voxels, const float* e, float* rmse,
+                                     double* sumsq, void* stream);
+
 /* ------------------------------------------------------- batched SBB-NNLS */
 
 /*

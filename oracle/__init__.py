@@ -57,6 +57,10 @@ def _load():
                                         ctypes.POINTER(_SbbState), P]
         lib.oracle_sbb_solve.argtypes = [i64, P, P, P, P, i32, P, i64, i64, P, P, dbl, i32, i64,
                                          ctypes.POINTER(_SbbState), P]
+        lib.oracle_voxel_rmse.argtypes = [i32, i64, P, P]
+        lib.oracle_voxel_rmse.restype = dbl
+        lib.oracle_prune.argtypes = [i64, P, ctypes.c_float, P, P]
+        lib.oracle_prune.restype = i64
         _lib = lib
     return _lib
 
@@ -195,3 +199,21 @@ def sbb_solve(phi: Phi, D, b, w, n_theta, n_voxels, n_fasc, max_iter, tol=0.0, e
 def problem_signal(phi: Phi, D, w_true, noise, n_theta, n_voxels):
     """b = M w_true + noise, rounded to float32 (the measured, demeaned signal)."""
     return (dsc(phi, D, w_true, n_theta, n_voxels) + _f64(noise)).astype(np.float32)
+
+
+def voxel_rmse(e, n_theta: int, n_voxels: int):
+    """(rmse [Nv], Σ e²): per-voxel root-mean-square of a residual over θ."""
+    ed = _f64(e)
+    assert ed.size == n_theta * n_voxels
+    rmse = np.empty(n_voxels, np.float64)
+    total = _load().oracle_voxel_rmse(n_theta, n_voxels, _p(ed), _p(rmse))
+    return rmse, float(total)
+
+
+def prune(w, threshold: float = 0.0):
+    """(keep mask uint8 [Nf], kept fascicle ids int32): fascicles with w > threshold."""
+    wf = np.ascontiguousarray(w, dtype=np.float32)
+    keep = np.empty(wf.size, np.uint8)
+    kept = np.empty(max(wf.size, 1), np.int32)
+    n = _load().oracle_prune(wf.size, _p(wf), float(threshold), _p(keep), _p(kept))
+    return keep, kept[:n].copy()

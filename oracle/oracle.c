@@ -14,6 +14,10 @@
  *   oracle_wc          g = M^T r, g[f] = Σ_k val_k Σ_θ D[θ,a_k] r[θ,v_k] [f_k = f]
  *   oracle_sbb_step    one SBB-NNLS iteration (Eq. 5-8, Algorithm 1)
  *   oracle_grad_D      dL/dD for L = ½‖r - M(D) w‖²
+ *   oracle_voxel_rmse  per-voxel prediction error sqrt(Σ_θ e[θ,v]² / Nθ) of a residual
+ *                      (the error by which LiFE evaluates a connectome, Sec. 2.1)
+ *   oracle_prune       the pruned connectome: fascicles with weight above a threshold
+ *                      (LiFE keeps the fascicles of positive weight, Sec. 1 and Sec. 2.1)
  *
  * Layouts: D is column-major D[θ + Nθ·a]; signals y, r, b, e are column-major
  * [θ + Nθ·v].  All arithmetic is double precision; compile with -ffp-contract=off.
@@ -245,4 +249,30 @@ void oracle_sbb_solve(int64_t n, const int32_t* atom, const int32_t* voxel, cons
                       oracle_sbb_state* st, double* work) {
     for (int64_t i = 0; i < max_iter && !st->converged; ++i)
         oracle_sbb_step(n, atom, voxel, fasc, val, nt, D, nv, nf, b, w, tol, eq7_on_even, st, work);
+}
+
+/* ------------------------------------------------------------ evaluation */
+
+/* Per-voxel root-mean-square of a residual e = M w - b over the Nθ directions:
+ * rmse[v] = sqrt( Σ_θ e[θ,v]^2 / Nθ ).  Returns Σ over all (θ,v) of e^2. */
+double oracle_voxel_rmse(int nt, int64_t nv, const double* e, double* rmse) {
+    double total = 0.0;
+    for (int64_t v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += e[t + (int64_t)nt * v] * e[t + (int64_t)nt * v];
+        rmse[v] = sqrt(s / nt);
+        total += s;
+    }
+    return total;
+}
+
+/* Pruned connectome: keep[f] = 1 when w[f] > threshold (a NaN weight is not
+ * kept), kept[] = the kept fascicles in increasing order.  Returns their number. */
+int64_t oracle_prune(int64_t nf, const float* w, float threshold, uint8_t* keep, int32_t* kept) {
+    int64_t n = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+        keep[f] = w[f] > threshold ? 1 : 0;
+        if (keep[f]) kept[n++] = (int32_t)f;
+    }
+    return n;
 }

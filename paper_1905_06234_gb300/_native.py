@@ -29,7 +29,7 @@ EXPORTS = [
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_batch_create", "life_batch_free", "life_batch_get_info",
     "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
     "life_index_autotune", "life_selftest_bounded_wait", "life_check_device_status", "life_last_error",
-    "life_version",
+    "life_version", "life_prune", "life_voxel_rmse",
 ]
 
 
@@ -115,6 +115,8 @@ def load(build_if_missing: bool = False):
     L.life_index_autotune.argtypes = [P, P]
     L.life_selftest_bounded_wait.argtypes = [i64, P]
     L.life_check_device_status.argtypes = [P]
+    L.life_prune.argtypes = [i32, P, ctypes.c_float, P, P, P, P, P]
+    L.life_voxel_rmse.argtypes = [i32, i32, P, P, P, P]
     L.life_last_error.restype = ctypes.c_char_p
     L.life_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -490,3 +492,40 @@ def life_batch_solve(batch: LifeBatch, D, bs, ws, max_iter, st, workspace, tol=0
 def life_selftest_bounded_wait(limit_ns: int):
     """Runs a wait that cannot complete, bounded to limit_ns (see include/life.h)."""
     _check(load().life_selftest_bounded_wait(int(limit_ns), _stream()))
+
+
+# ------------------------------------------------------ connectome evaluation
+
+def life_prune(w, threshold=0.0):
+    """(keep uint8 [Nf], kept int32 ids in increasing order, w_pruned) for w > threshold."""
+    _need(w, torch.float32, w.numel(), "w")
+    nf = int(w.numel())
+    keep = torch.empty(nf, dtype=torch.uint8, device=w.device)
+    kept = torch.empty(max(nf, 1), dtype=torch.int32, device=w.device)
+    n_kept = torch.empty(1, dtype=torch.int64, device=w.device)
+    w_pruned = torch.empty(nf, dtype=torch.float32, device=w.device)
+    _check(load().life_prune(nf, _ptr(w), float(threshold), _ptr(keep), _ptr(kept), _ptr(n_kept), _ptr(w_pruned),
+                             _stream()))
+    return keep, kept[:int(n_kept.item())], w_pruned
+
+
+def life_voxel_rmse(e, n_theta: int, n_voxels: int):
+    """(rmse float32 [Nv], Σ e² as a float64 device tensor) of a residual e = M w − b."""
+    _need(e, torch.float32, n_theta * n_voxels, "e")
+    rmse = torch.empty(n_voxels, dtype=torch.float32, device=e.device)
+    ss = torch.empty(1, dtype=torch.float64, device=e.device)
+    _check(load().life_voxel_rmse(int(n_theta), int(n_voxels), _ptr(e), _ptr(rmse), _ptr(ss), _stream()))
+    return rmse, ss
+
+
+def evaluate_connectome(index: LifeIndex, D, w, b, threshold=0.0):
+    """LiFE's evaluation of a fitted connectome: the pruned model (fascicles with
+    w > threshold) and its per-voxel prediction error.  Returns a dict with the
+    kept fascicle ids, the pruned weights, the residual of the pruned model
+    e = M w_pruned − b, its per-voxel RMSE and the global RMSE."""
+    keep, kept, w_pruned = life_prune(w, threshold)
+    e, _ = life_dsc(index, D, w_pruned, b=b)
+    rmse, ss = life_voxel_rmse(e, index.n_theta, index.n_voxels)
+    n = index.n_theta * index.n_voxels
+    return dict(keep=keep, kept=kept, w_pruned=w_pruned, e=e, rmse=rmse,
+                global_rmse=float((ss / max(n, 1)).sqrt().item()))

@@ -325,3 +325,54 @@ def test_gradients_finite_differences():
 
     fd = (loss_lam(p.lam + h) - loss_lam(p.lam - h)) / (2 * h)
     assert abs(fd - glam) <= 1e-5 * max(1.0, abs(glam))
+
+
+# ------------------------------------------------------------ evaluation
+
+
+def _evaluate_golden():
+    from tests._golden import read_sections
+    s = read_sections("evaluate_small.txt")
+    nt, nv = (int(x) for x in s["dims"][0])
+    flat = lambda k: np.array([x for row in s[k] for x in row], np.float64)
+    return nt, nv, s, flat
+
+
+def test_voxel_rmse_golden():
+    nt, nv, s, flat = _evaluate_golden()
+    rmse, total = oracle.voxel_rmse(flat("e"), nt, nv)
+    np.testing.assert_allclose(rmse, flat("rmse"), rtol=1e-15, atol=0)
+    assert total == flat("total")[0]
+
+
+def test_voxel_rmse_invariants():
+    rng = np.random.default_rng(3)
+    nt, nv = 7, 50
+    e = rng.standard_normal(nt * nv)
+    rmse, total = oracle.voxel_rmse(e, nt, nv)
+    # Σ_v Nθ·rmse² is the total sum of squares; scaling e scales rmse by |k|
+    assert abs(nt * (rmse ** 2).sum() - total) <= 1e-12 * total
+    assert abs(total - float(e @ e)) <= 1e-12 * total
+    np.testing.assert_allclose(oracle.voxel_rmse(-2.5 * e, nt, nv)[0], 2.5 * rmse, rtol=1e-14)
+    # a voxel whose residual is the constant c over θ has rmse |c|
+    c = np.repeat(rng.standard_normal(nv), nt)
+    np.testing.assert_allclose(oracle.voxel_rmse(c, nt, nv)[0], np.abs(c[::nt]), rtol=1e-15)
+
+
+def test_prune_golden():
+    _, _, s, flat = _evaluate_golden()
+    w = flat("w").astype(np.float32)
+    for thr, key in ((0.0, "kept_t0"), (0.25, "kept_t025")):
+        keep, kept = oracle.prune(w, thr)
+        assert kept.tolist() == [int(x) for x in flat(key)]
+        assert keep.tolist() == [1 if i in kept else 0 for i in range(w.size)]
+
+
+def test_prune_invariants():
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal(1000).astype(np.float32)
+    w[rng.random(1000) < 0.3] = 0.0
+    keep, kept = oracle.prune(w, 0.0)
+    assert (np.diff(kept) > 0).all() and keep.sum() == kept.size
+    assert (w[kept] > 0).all() and not (w[keep == 0] > 0).any()
+    assert oracle.prune(np.zeros(0, np.float32))[1].size == 0
