@@ -59,7 +59,10 @@ typedef struct {
                               (0 = 4, or the largest that fits in shared memory) */
     int32_t autotune;      /* 1 = choose brick_dim and wc_groups by timing candidates on this GPU
                               (TC path; results cached per problem shape for the process) */
-    int32_t reserved[3];   /* must be zero */
+    int32_t sparse_dsc;    /* TC path: 1 = the index also keeps a live-entry DSC stream, and a DSC whose
+                              input is sparse streams only the entries of fascicles with a non-zero input
+                              (see life_dsc); 0 (default) = every DSC streams all entries */
+    int32_t reserved[2];   /* must be zero */
 } life_opts;
 
 typedef struct life_index_s* life_index;
@@ -155,10 +158,30 @@ LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, 
  *  b      float32 [Nθ·Nv] or NULL
  *  y      float32 [Nθ·Nv] output, or NULL to compute only `sumsq`
  *  sumsq  double [1] output, or NULL: Σ over all (θ,v) of the written y, in FP64
+ * Sparse w (Sec. 4.2.1: a zero weight contributes nothing, and SBB-NNLS keeps
+ * many weights at exactly zero): on a TC index built with sparse_dsc, the call
+ * checks on the device whether w's non-zeros lie inside the live set of the
+ * index's live-entry stream; if w is sparse enough (at most 92 % of the brick
+ * table slots non-zero) it streams only the live entries, rebuilding that stream
+ * for w's support when it is stale or much larger than needed.  The result is
+ * that of the full stream up to the association of FP32 run sums.
  * Errors: LIFE_EINVAL when D, w or both y and sumsq are NULL.
  */
 LIFE_API life_status life_dsc(life_index idx, const float* D, const float* w, const float* b, float* y,
                      double* sumsq, void* stream);
+
+/*
+ * Counters of the live-entry DSC stream of a TC index (all zero when the index
+ * has none).  Host output out[6]:
+ *   [0] DSC calls that went through the device-side choice of stream
+ *   [1] of those, calls that streamed the live (compacted) entries only
+ *   [2] rebuilds of the live-entry stream
+ *   [3] entries of the live-entry stream as last built
+ *   [4] entries of the full stream
+ *   [5] live brick-table slots when the live-entry stream was last built
+ * Synchronizes `stream`.
+ */
+LIFE_API life_status life_index_sparse_stats(life_index idx, int64_t* out, void* stream);
 
 /*
  * WC, g = M^T r (Sec. 4 "WC"; the transpose of Eq. 1):

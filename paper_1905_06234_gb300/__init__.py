@@ -11,7 +11,7 @@ from ._native import (  # noqa: F401
     life_sbb_workspace_bytes, life_sbbnnls_solve, life_sbbnnls_step, life_version, life_wc, load, new_sbb_state,
     new_sbb_workspace, read_sbb_state, LifeBatch, life_batch_create, life_batch_solve, life_index_autotune,
     new_batch_states, new_batch_workspace, read_batch_states, life_selftest_bounded_wait,
-    life_prune, life_voxel_rmse, evaluate_connectome,
+    life_prune, life_voxel_rmse, evaluate_connectome, life_index_sparse_stats,
 )
 from .autograd import LifeDSC, LifeDictionary, dictionary, dsc  # noqa: F401
 from .problem import index_from_arrays, upload_problem  # noqa: F401

@@ -29,7 +29,7 @@ EXPORTS = [
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_batch_create", "life_batch_free", "life_batch_get_info",
     "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
     "life_index_autotune", "life_selftest_bounded_wait", "life_check_device_status", "life_last_error",
-    "life_version", "life_prune", "life_voxel_rmse",
+    "life_version", "life_prune", "life_voxel_rmse", "life_index_sparse_stats",
 ]
 
 
@@ -41,7 +41,8 @@ class LifeError(RuntimeError):
 
 class life_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("brick_dim", ctypes.c_int32),
-                ("wc_groups", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("wc_groups", ctypes.c_int32), ("autotune", ctypes.c_int32), ("sparse_dsc", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class life_index_info(ctypes.Structure):
@@ -115,6 +116,7 @@ def load(build_if_missing: bool = False):
     L.life_index_autotune.argtypes = [P, P]
     L.life_selftest_bounded_wait.argtypes = [i64, P]
     L.life_check_device_status.argtypes = [P]
+    L.life_index_sparse_stats.argtypes = [P, P, P]
     L.life_prune.argtypes = [i32, P, ctypes.c_float, P, P, P, P, P]
     L.life_voxel_rmse.argtypes = [i32, i32, P, P, P, P]
     L.life_last_error.restype = ctypes.c_char_p
@@ -200,7 +202,8 @@ class LifeIndex:
 # ------------------------------------------------------------------ the ABI
 
 def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc, voxel_ijk=None,
-                     precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0, wc_groups=0, autotune=False) -> LifeIndex:
+                     precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0, wc_groups=0, autotune=False,
+                     sparse_dsc=False) -> LifeIndex:
     L = load()
     n = int(atom.numel())
     for t, dt, nm in ((atom, torch.int32, "atom"), (voxel, torch.int32, "voxel"), (fasc, torch.int32, "fasc"),
@@ -209,7 +212,7 @@ def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc,
     if voxel_ijk is not None:
         _need(voxel_ijk, torch.int32, 3 * n_voxels, "voxel_ijk")
     opts = life_opts(precision=int(precision), algo=int(algo), brick_dim=int(brick_dim), wc_groups=int(wc_groups),
-                     autotune=1 if autotune else 0)
+                     autotune=1 if autotune else 0, sparse_dsc=1 if sparse_dsc else 0)
     h = ctypes.c_void_p()
     _check(L.life_build_index(_ptr(atom), _ptr(voxel), _ptr(fasc), _ptr(val), n, int(n_theta), int(n_atoms),
                               int(n_voxels), int(n_fasc), _ptr(voxel_ijk), ctypes.byref(opts), _stream(),
@@ -362,6 +365,14 @@ def life_sbbnnls_step(index: LifeIndex, D, b, w, st, workspace, tol=0.0, eq7_on_
 def life_sbbnnls_solve(index: LifeIndex, D, b, w, max_iter, st, workspace, tol=0.0, eq7_on_even=True):
     _check(load().life_sbbnnls_solve(index.handle, _ptr(D), _ptr(b), _ptr(w), int(max_iter), float(tol),
                                      1 if eq7_on_even else 0, _ptr(st), _aligned(workspace), _stream()))
+
+
+def life_index_sparse_stats(index: LifeIndex) -> dict:
+    """Counters of the live-entry DSC stream (see include/life.h)."""
+    out = (ctypes.c_int64 * 6)()
+    _check(load().life_index_sparse_stats(index.handle, out, _stream()))
+    keys = ("calls", "compact_calls", "rebuilds", "live_entries", "entries", "live_slots")
+    return dict(zip(keys, (int(x) for x in out)))
 
 
 def life_check_device_status():

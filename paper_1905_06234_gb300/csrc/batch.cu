@@ -252,7 +252,7 @@ extern "C" life_status life_batch_create(int32_t n, const life_index* idx, const
     }
     life_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) {
             set_error("life_batch_create: reserved option fields must be zero");
             return LIFE_EINVAL;

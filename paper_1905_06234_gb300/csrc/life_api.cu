@@ -147,7 +147,11 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     }
     life_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 3; ++i)
+    if (o.sparse_dsc < 0 || o.sparse_dsc > 1) {
+        set_error("life_build_index: sparse_dsc must be 0 or 1");
+        return LIFE_EINVAL;
+    }
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) {
             set_error("life_build_index: reserved option fields must be zero");
             return LIFE_EINVAL;
@@ -182,6 +186,7 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     ix->precision = o.precision;
     ix->brick_dim = o.brick_dim > 0 ? o.brick_dim : 8;
     ix->wc_groups = o.wc_groups;
+    ix->sparse_dsc = o.sparse_dsc;
     life_status st = build_index_layouts(ix, atom, voxel, fasc, val, voxel_ijk, o.algo, s);
     if (st == LIFE_OK && o.autotune) st = autotune_tc(ix, s);
     if (st != LIFE_OK) {
@@ -224,7 +229,9 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
                             &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
                             &idx->tile.va, &idx->tile.soff, &idx->tile.fl, &idx->tile.val, &idx->tile.wkey,
                             &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->tile.wb_src,
-                            &idx->tile.wb_ptr, &idx->tile.wb, &idx->tile.brick_cv, &idx->tile.tile_amax, &idx->red};
+                            &idx->tile.wb_ptr, &idx->tile.wb, &idx->tile.brick_cv, &idx->tile.tile_amax, &idx->red,
+                            &idx->tile.c_soff, &idx->tile.c_fl, &idx->tile.c_val, &idx->tile.c_chunk_end,
+                            &idx->tile.wb_live, &idx->tile.sparse_ctl, &idx->tile.tile_brick};
     int64_t tot = 0;
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;
@@ -288,6 +295,14 @@ extern "C" life_status life_dsc(life_index idx, const float* D, const float* w, 
     LIFE_TRY(spmv_dsc(idx, D, w, b, y, partial, &np, nullptr, GATE_NONE, s));
     if (sumsq) LIFE_TRY(reduce_partials(partial, np, sumsq, s));
     return LIFE_OK;
+}
+
+extern "C" life_status life_index_sparse_stats(life_index idx, int64_t* out, void* stream) {
+    if (!idx || !out) {
+        set_error("life_index_sparse_stats: null argument");
+        return LIFE_EINVAL;
+    }
+    return sparse_stats(idx, out, (cudaStream_t)stream);
 }
 
 extern "C" life_status life_wc(life_index idx, const float* D, const float* r, float* g, double* sumsq,

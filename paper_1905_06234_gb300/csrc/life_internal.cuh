@@ -153,11 +153,21 @@ struct TileLayout {
     // before each DSC launch, into wb[wb_ptr[b] ..) (16-byte aligned, padded to a
     // multiple of 4 floats) so a CTA loads a brick's table with one bulk copy
     int64_t wb_total = 0;
+    int64_t n_brick_slots = 0;  // real (unpadded) slots of the brick weight tables
     DevBuf wb_src;           // int32 [wb_total]: global fascicle of each slot (0 for padding)
     DevBuf wb_ptr;           // int32 [n_bricks + 1], multiples of 4
     DevBuf wb;               // float [wb_total]: gathered weights (rewritten by every DSC call)
     // WC fixed-point tables: per brick, an upper bound on Σ|val| over the entries of
     // any one brick-local fascicle; per tile, the bits of max |r| over its voxels
+    // Live-entry DSC stream (sparse-w-aware DSC): the DSC stream restricted to the
+    // entries of a live set of brick-local fascicles, same (tile, sub-chunk) structure
+    bool sparse = false;     // the index keeps and may use the compacted stream
+    DevBuf c_soff, c_fl, c_val;  // uint16, uint16, bf16 [n_nnz padded]
+    DevBuf c_chunk_end;      // int32 [n_tiles * kp/128]: each 128-atom chunk's live entries occupy
+                             // the start of the chunk's own range: [chunk begin, c_chunk_end)
+    DevBuf wb_live;          // uint8 [wb_total]: 1 for slots in the live set
+    DevBuf sparse_ctl;       // device decision state of the compacted stream
+    DevBuf tile_brick;       // int32 [n_tiles] brick of each tile
     DevBuf brick_cv;         // float [n_bricks]: (largest entry count of a fascicle) x (largest |val|)
     DevBuf tile_amax;        // uint32 [n_tiles * 4]: bits of max |r| per tile row quarter (written by
                              // every DSC that stores y, and by WC calls whose r did not come from one)
@@ -198,6 +208,7 @@ struct life_index_s {
     int64_t nnz_raw = 0, nnz = 0;
     int32_t precision = LIFE_FP32, algo = LIFE_ALGO_SIMT, brick_dim = 8;
     int32_t wc_groups = 0;      // TC WC scatter groups (0 = the largest that fits)
+    int32_t sparse_dsc = 0;     // TC: keep a live-entry DSC stream (sparse-w-aware DSC)
     int32_t tuned = 0;          // 1 once the autotuner chose brick_dim and wc_groups
     int32_t key_bits_v = 0, key_bits_a = 0, key_bits_f = 0;
     int device = 0;
@@ -269,6 +280,8 @@ life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int
 // (rebuilds the tile layout); a no-op on the CUDA-core path.
 life_status autotune_tc(life_index_s* ix, cudaStream_t s);
 int wc_effective_groups(const life_index_s* ix);
+// Counters of the live-entry DSC stream (life_index_sparse_stats).
+life_status sparse_stats(life_index_s* ix, int64_t* out, cudaStream_t s);
 life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s);
 
 // Builds and instantiates a graph made of one conditional WHILE node whose body

@@ -91,30 +91,250 @@ __global__ void brick_fasc_kernel(const uint64_t* __restrict__ key2, int64_t m, 
     }
 }
 
-// wb_src[wb_ptr[b] + i] = brick_fasc[brick_fasc_ptr[b] + i], padding slots 0 (one block per brick).
+// wb_src[wb_ptr[b] + i] = brick_fasc[brick_fasc_ptr[b] + i], padding slots -1 (one block per brick).
 __global__ void wb_src_kernel(const int32_t* __restrict__ bptr, const int32_t* __restrict__ bfasc,
                               const int32_t* __restrict__ wptr, int32_t nb, int32_t* __restrict__ wsrc) {
     for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const int32_t f0 = bptr[b], n = bptr[b + 1] - f0, o = wptr[b], np = wptr[b + 1] - o;
-        for (int32_t i = threadIdx.x; i < np; i += blockDim.x) wsrc[o + i] = i < n ? bfasc[f0 + i] : 0;
+        for (int32_t i = threadIdx.x; i < np; i += blockDim.x) wsrc[o + i] = i < n ? bfasc[f0 + i] : -1;
     }
 }
 
-// wb[j] = w[wb_src[j]]: the DSC's brick weight tables for this call's w.
-// (n is a multiple of 4 and both arrays are 16-byte aligned: each thread moves 4
-// slots per step with one 16-byte load of indices, four independent gathers and
-// one 16-byte store.)
+__device__ __forceinline__ float gather_slot(const float* __restrict__ w, int32_t id) {
+    return id >= 0 ? __ldg(w + id) : 0.0f;
+}
+
+// wb[j] = w[wb_src[j]] (0 for padding slots): the DSC's brick weight tables for
+// this call's w.  (n is a multiple of 4 and both arrays are 16-byte aligned: each
+// thread moves 4 slots per step with one 16-byte load of indices, four
+// independent gathers and one 16-byte store.)
 __global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
                                  float* __restrict__ wb) {
     const int64_t n4 = n >> 2;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
         const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
         float4 v;
-        v.x = __ldg(w + id.x);
-        v.y = __ldg(w + id.y);
-        v.z = __ldg(w + id.z);
-        v.w = __ldg(w + id.w);
+        v.x = gather_slot(w, id.x);
+        v.y = gather_slot(w, id.y);
+        v.z = gather_slot(w, id.z);
+        v.w = gather_slot(w, id.w);
         reinterpret_cast<float4*>(wb)[j] = v;
+    }
+}
+
+// ------------------------------------------------- live-entry DSC stream
+//
+// The sparse-w-aware DSC (Sec. 4.2.1: an entry whose weight is zero contributes
+// nothing, and SBB-NNLS iterates keep many weights at exactly zero).  Besides the
+// full stream, the index keeps a compacted copy holding only the entries of a
+// live set L of brick-local fascicles, with the same (tile, 32-atom sub-chunk)
+// structure.  Every DSC call checks on the device whether the input's support
+// lies inside L ("stale" otherwise); a small decision kernel then picks the full
+// or the compacted stream for this call, and may rebuild the compacted stream
+// (L := the input's support) when the input is sparse enough and the stored
+// copy is stale or has become much larger than needed.  Dropping zero-weight
+// entries only removes exact +0 terms from each run sum, so both streams give
+// the same S values up to the association of a run's FP32 sum.
+
+enum : uint32_t { DSC_MODE_NONE = 0, DSC_MODE_FULL = 1, DSC_MODE_COMPACT = 2 };
+
+struct SparseCtl {
+    unsigned long long n_live;        // real slots with x != 0 seen by this call's gather
+    unsigned long long n_live_cmp;    // that count when the compacted stream was built
+    unsigned long long n_compactions; // compacted-stream rebuilds so far
+    unsigned long long n_compact_calls;  // DSC calls that streamed the compacted entries
+    unsigned long long n_calls;       // DSC calls that went through the decision
+    uint32_t stale;                   // some slot with x != 0 lies outside L
+    uint32_t mode;                    // DSC_MODE_* of the current call
+    uint32_t compact_now;             // the current call rebuilds the compacted stream
+    uint32_t have;                    // a compacted stream exists
+    uint32_t gather_done;             // blocks of the gather finished (the last one decides)
+};
+
+// Thresholds of the decision: the compacted stream is used only while the live
+// slots are at most DENSE_FRAC of all slots, and rebuilt once the live count has
+// fallen below SHRINK_FRAC of the count it was built for.
+constexpr double DENSE_FRAC = 0.92;
+constexpr double SHRINK_FRAC = 0.9;
+
+// The decision for this call, taken by the last block of the gather once every
+// block's counts are in.
+__device__ void dsc_decide(SparseCtl* c, unsigned long long n_slots, int allow, const life_sbb_state* gate,
+                           int gate_mode) {
+    volatile SparseCtl* vc = c;
+    const unsigned long long nl = vc->n_live;
+    const bool stale = vc->stale != 0u;
+    c->n_live = 0ull;  // the next gather counts from zero
+    c->stale = 0u;
+    if (gate_skip(gate, gate_mode)) {
+        c->mode = DSC_MODE_NONE;
+        c->compact_now = 0u;
+        return;
+    }
+    uint32_t mode, cmp = 0u;
+    if ((double)nl > DENSE_FRAC * (double)n_slots) {
+        mode = DSC_MODE_FULL;
+    } else if (allow && (!c->have || stale || (double)nl < SHRINK_FRAC * (double)c->n_live_cmp)) {
+        cmp = 1u;
+        mode = DSC_MODE_COMPACT;
+        c->have = 1u;
+        c->n_live_cmp = nl;
+        c->n_compactions += 1ull;
+    } else {
+        mode = stale ? DSC_MODE_FULL : DSC_MODE_COMPACT;
+    }
+    c->mode = mode;
+    c->compact_now = cmp;
+    c->n_calls += 1ull;
+    if (mode == DSC_MODE_COMPACT) c->n_compact_calls += 1ull;
+}
+
+// wb gather plus the liveness bookkeeping: the number of real slots with a
+// non-zero value (NaN counts as non-zero) and whether one of them lies outside
+// L; the last block to finish takes the call's decision.
+constexpr int GATHER_THREADS = 256;
+
+__global__ void __launch_bounds__(GATHER_THREADS) wb_gather_live_kernel(const int32_t* __restrict__ wsrc, int64_t n,
+                                                                        const float* __restrict__ w,
+                                                                        float* __restrict__ wb,
+                                                                        const uint8_t* __restrict__ live,
+                                                                        SparseCtl* __restrict__ ctl,
+                                                                        unsigned long long n_slots, int allow,
+                                                                        const life_sbb_state* gate, int gate_mode) {
+    __shared__ unsigned int blk_n, blk_stale, last;
+    if (threadIdx.x == 0) blk_n = blk_stale = 0u;
+    __syncthreads();
+    const int64_t n4 = n >> 2;
+    unsigned int cnt = 0u, stale = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
+        const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
+        const uchar4 lv = __ldg(reinterpret_cast<const uchar4*>(live) + j);
+        float4 v;
+        v.x = gather_slot(w, id.x);
+        v.y = gather_slot(w, id.y);
+        v.z = gather_slot(w, id.z);
+        v.w = gather_slot(w, id.w);
+        reinterpret_cast<float4*>(wb)[j] = v;
+        // padding slots hold 0 and never count
+        const bool nx = v.x != 0.0f, ny = v.y != 0.0f, nz = v.z != 0.0f, nw = v.w != 0.0f;
+        cnt += (unsigned)nx + (unsigned)ny + (unsigned)nz + (unsigned)nw;
+        stale |= (nx && !lv.x) || (ny && !lv.y) || (nz && !lv.z) || (nw && !lv.w);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        stale |= __shfl_xor_sync(0xffffffffu, stale, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&blk_n, cnt);
+        atomicOr(&blk_stale, stale);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blk_n) atomicAdd(&ctl->n_live, (unsigned long long)blk_n);
+        if (blk_stale) atomicOr(&ctl->stale, 1u);
+        __threadfence();
+        last = atomicAdd(&ctl->gather_done, 1u) == gridDim.x - 1 ? 1u : 0u;
+        if (last) {
+            __threadfence();
+            dsc_decide(ctl, n_slots, allow, gate, gate_mode);
+            ctl->gather_done = 0u;
+        }
+    }
+}
+
+struct CompactArgs {
+    const int32_t* sub_ptr;
+    const int32_t* tile_brick;
+    const int32_t* wb_ptr;
+    const float* wb;
+    const uint16_t* soff;
+    const uint16_t* fl;
+    const __nv_bfloat16* val;
+    uint8_t* wb_live;
+    uint16_t* c_soff;
+    uint16_t* c_fl;
+    __nv_bfloat16* c_val;
+    int32_t* c_chunk_end;   // [n_tiles * chunks per tile] end of each chunk's live entries
+    SparseCtl* ctl;
+    int n_sub, n_c;         // sub-chunks and 128-atom chunks per tile
+    int64_t n_chunks, wb_total;
+};
+
+constexpr int CMP_THREADS = 256;
+
+__device__ __forceinline__ uint32_t u16_of(const uint4& v, int e) {
+    const uint32_t w = e < 2 ? v.x : e < 4 ? v.y : e < 6 ? v.z : v.w;
+    return (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+// Live flags (bit e) of the 8 entries of the slot at `base` inside [beg, end).
+__device__ __forceinline__ uint32_t slot_live(const uint4& flv, int base, int beg, int end, const float* wbb) {
+    uint32_t m = 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = base + e;
+        if (j >= beg && j < end && wbb[u16_of(flv, e) & 0x7FFFu] != 0.0f) m |= 1u << e;
+    }
+    return m;
+}
+
+// Rebuild of the live-entry stream, one warp per 128-atom chunk (8 entries per
+// lane per step).  A chunk's live entries are written in order to the start of
+// the chunk's own range [beg, end) of the compacted arrays, and its end is
+// recorded: no scan is needed and the DSC reads [beg, c_chunk_end).  An entry
+// continues a run when the previous LIVE entry of the chunk has the same S offset
+// (the same (atom, row)): runs are contiguous in the sorted stream, so that is
+// the run it belonged to.  L := the slots whose gathered value is non-zero.
+__global__ void __launch_bounds__(CMP_THREADS) cmp_rebuild_kernel(CompactArgs C) {
+    if (!C.ctl->compact_now) return;
+    for (int64_t j = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x; j < C.wb_total; j += (int64_t)gridDim.x * CMP_THREADS)
+        C.wb_live[j] = C.wb[j] != 0.0f ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const int64_t warps = (int64_t)gridDim.x * (CMP_THREADS / 32);
+    for (int64_t ch = blockIdx.x * (int64_t)(CMP_THREADS / 32) + (threadIdx.x >> 5); ch < C.n_chunks; ch += warps) {
+        const int64_t t = ch / C.n_c, c = ch - t * C.n_c;
+        const float* wbb = C.wb + C.wb_ptr[C.tile_brick[t]];
+        const int beg = C.sub_ptr[t * C.n_sub + c * (128 / SUB)], end = C.sub_ptr[t * C.n_sub + (c + 1) * (128 / SUB)];
+        int out = beg;
+        uint32_t prev = 0xFFFFFFFFu;  // S offset of the last live entry so far (none)
+        for (int base = (beg & ~7) + lane * 8; __any_sync(0xffffffffu, base < end); base += 256) {
+            uint4 flv = make_uint4(0u, 0u, 0u, 0u), sov = flv, vav = flv;
+            uint32_t m = 0u;
+            if (base < end) {
+                flv = __ldg(reinterpret_cast<const uint4*>(C.fl + base));
+                sov = __ldg(reinterpret_cast<const uint4*>(C.soff + base));
+                vav = __ldg(reinterpret_cast<const uint4*>(C.val) + (base >> 3));
+                m = slot_live(flv, base, beg, end, wbb);
+            }
+            const int n = __popc(m);
+            int pre = n;  // inclusive prefix of the live counts over the lanes
+            for (int x = 1; x < 32; x <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, pre, x);
+                if (lane >= x) pre += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            // S offset of this lane's last live entry, and the previous live entry before this lane
+            const uint32_t last_so = m ? u16_of(sov, 31 - __clz(m)) : 0u;
+            const uint32_t has = __ballot_sync(0xffffffffu, m != 0u);
+            const uint32_t lower = has & below;
+            const uint32_t from = __shfl_sync(0xffffffffu, last_so, lower ? 31 - __clz(lower) : lane);
+            uint32_t p = lower ? from : prev;
+            int q = out + pre - n;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (!((m >> e) & 1u)) continue;
+                const uint32_t so = u16_of(sov, e);
+                C.c_soff[q] = (uint16_t)so;
+                C.c_fl[q] = (uint16_t)((u16_of(flv, e) & 0x7FFFu) | (p == so ? CONT : 0u));
+                reinterpret_cast<uint16_t*>(C.c_val)[q] = (uint16_t)u16_of(vav, e);
+                p = so;
+                ++q;
+            }
+            if (has) prev = __shfl_sync(0xffffffffu, last_so, 31 - __clz(has));
+            out += total;
+        }
+        if (lane == 0) C.c_chunk_end[ch] = out;
     }
 }
 
@@ -440,6 +660,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         std::vector<int32_t> wptr(H.n_bricks + 1, 0);
         for (int64_t b = 0; b < H.n_bricks; ++b) wptr[b + 1] = wptr[b] + (hbptr[b + 1] - hbptr[b] + 3) / 4 * 4;
         L.wb_total = wptr[H.n_bricks];
+        L.n_brick_slots = hbptr[H.n_bricks];
         LIFE_TRY(upload(L.wb_ptr, wptr, s));
         LIFE_TRY(L.wb_src.alloc(sizeof(int32_t) * std::max<int64_t>(L.wb_total, 4)));
         LIFE_TRY(L.wb.alloc(sizeof(float) * std::max<int64_t>(L.wb_total, 4)));
@@ -510,6 +731,32 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     }
     LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
     LIFE_TRY(upload(L.brick_tile_ptr, H.brick_tile_ptr, s));
+    // live-entry DSC stream: allocated at full size, filled on demand by a DSC call
+    L.sparse = ix->sparse_dsc != 0 && ix->batch.vox_group.empty();
+    if (L.sparse) {
+        LIFE_TRY(L.c_soff.alloc(sizeof(uint16_t) * m_pad));
+        LIFE_TRY(L.c_fl.alloc(sizeof(uint16_t) * m_pad));
+        LIFE_TRY(L.c_val.alloc(sizeof(__nv_bfloat16) * m_pad));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.c_soff.p, 0, sizeof(uint16_t) * m_pad, s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.c_fl.p, 0, sizeof(uint16_t) * m_pad, s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.c_val.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+        const int64_t n_chunks = std::max<int64_t>(H.n_tiles * (L.kp / 128), 1);
+        LIFE_TRY(L.c_chunk_end.alloc(sizeof(int32_t) * n_chunks));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.c_chunk_end.p, 0, sizeof(int32_t) * n_chunks, s));
+        LIFE_TRY(L.wb_live.alloc(std::max<int64_t>(L.wb_total, 4)));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.wb_live.p, 0, std::max<int64_t>(L.wb_total, 4), s));
+        LIFE_TRY(upload(L.tile_brick, H.tile_brick, s));
+        LIFE_TRY(L.sparse_ctl.alloc(sizeof(SparseCtl)));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.sparse_ctl.p, 0, sizeof(SparseCtl), s));
+    } else {
+        L.c_soff.release();
+        L.c_fl.release();
+        L.c_val.release();
+        L.c_chunk_end.release();
+        L.wb_live.release();
+        L.sparse_ctl.release();
+        L.tile_brick.release();
+    }
     LIFE_TRY(L.brick_cv.alloc(sizeof(float) * std::max<int64_t>(H.n_bricks, 1)));
     LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * 4 * std::max<int64_t>(H.n_tiles, 1)));
     if (H.n_bricks > 0) {
@@ -598,6 +845,10 @@ struct TcArgs {
     uint32_t* tile_amax;      // bits of max |r| per (tile, row quarter): written by DSC, read by WC
     const life_sbb_state* gate;
     int gate_mode;
+    const int32_t* chunk_end;  // DSC on the live-entry stream: end of each chunk's entries (else NULL:
+                               // a chunk ends where the next begins)
+    const SparseCtl* ctl;  // DSC: when set, the launch runs only if ctl->mode == want_mode
+    uint32_t want_mode;
     uint32_t* status;
     int nt, na, np, kp, n_sub, n_bricks, max_fb;
     int vec4;            // y / b / r pointers 16-byte aligned and Nθ % 4 == 0
@@ -664,6 +915,10 @@ __device__ __forceinline__ float bf16_at(const uint4& v, int e) { return __uint_
 
 __device__ __forceinline__ int chunk_beg(const TcArgs& A, int t, int c, int subs_per_chunk) {
     return A.sub_ptr[(int64_t)t * A.n_sub + (int64_t)c * subs_per_chunk];
+}
+
+__device__ __forceinline__ int chunk_end(const TcArgs& A, int t, int c, int subs_per_chunk, int n_c) {
+    return A.chunk_end ? A.chunk_end[(int64_t)t * n_c + c] : chunk_beg(A, t, c + 1, subs_per_chunk);
 }
 
 // Advances (r, brick, t, c) to the CTA's next chunk; false when none is left.
@@ -844,6 +1099,8 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     __shared__ int chunk_next[DSTAGE];  // next dynamically handed-out 256-entry block of the stage's chunk
     __shared__ double red[DSC_EPI_WARPS];
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
+    // full or compacted stream: of the two launches of a call, the one not chosen returns here
+    if (A.ctl && A.ctl->mode != A.want_mode) return;
     const bool write_y = A.out != nullptr && (A.bg.live || !(A.gate && A.gate_mode == GATE_ACTIVE_Y_EQ8 &&
                                                                A.gate->eq != 8));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -894,7 +1151,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
         const int b0 = live_brick(A, G, cta, r);
         if (b0 >= 0) {
             int brick = b0, t = A.brick_tile_ptr[brick], c = 0;
-            int beg = chunk_beg(A, t, 0, spc), end = chunk_beg(A, t, 1, spc);
+            int beg = chunk_beg(A, t, 0, spc), end = chunk_end(A, t, 0, spc, n_c);
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
             EntrySlot cur{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
@@ -934,7 +1191,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 int nbeg = 0, nend = 0;
                 if (nvalid) {
                     nbeg = chunk_beg(A, nt, nc, spc);
-                    nend = chunk_beg(A, nt, nc + 1, spc);
+                    nend = chunk_end(A, nt, nc, spc, n_c);
                 }
                 const int nbase = (nbeg & ~7) + tid * SLOT;
                 const bool nhave = nvalid && nbase < nend;
@@ -1658,16 +1915,66 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
     A.gate_mode = gate_mode;
     A.vec4 = (ix->nt % 4 == 0 && ((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) ? 1 : 0;
     const uint32_t smem = dsc_smem_bytes(A.np, A.kp, A.max_fb);
-    if (ix->tile.wb_total > 0) {
-        wb_gather_kernel<<<ix->num_sms * 8, 256, 0, s>>>(ix->tile.wb_src.as<int32_t>(), ix->tile.wb_total, w,
-                                                        ix->tile.wb.as<float>());
+    TileLayout& L = ix->tile;
+    const bool sparse = L.sparse && !bg.live && L.wb_total > 0 && L.n_nnz > 0;
+    if (L.wb_total > 0) {
+        if (sparse)
+            // the last block decides: full or compacted stream, rebuild or not (the
+            // SBB step's DSC of w never rebuilds: its support lies inside that of the
+            // previous projected gradient; every other call may)
+            wb_gather_live_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(
+                L.wb_src.as<int32_t>(), L.wb_total, w, L.wb.as<float>(), L.wb_live.as<uint8_t>(),
+                L.sparse_ctl.as<SparseCtl>(), (unsigned long long)L.n_brick_slots,
+                (gate && gate_mode == GATE_ACTIVE) ? 0 : 1, gate, gate_mode);
+        else
+            wb_gather_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(L.wb_src.as<int32_t>(), L.wb_total, w,
+                                                                      L.wb.as<float>());
         LIFE_CHECK_LAUNCH();
     }
     LIFE_CUDA_TRY(cudaFuncSetAttribute(dsc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
+    const int grid = (int)std::min<int64_t>(ix->num_sms, L.n_bricks);
+    if (n_partial) *n_partial = grid;
+    if (!sparse) {
+        dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+        LIFE_CHECK_LAUNCH();
+        return LIFE_OK;
+    }
+    SparseCtl* ctl = L.sparse_ctl.as<SparseCtl>();
+    if (!(gate && gate_mode == GATE_ACTIVE)) {
+        CompactArgs C{};
+        C.sub_ptr = L.sub_ptr.as<int32_t>();
+        C.tile_brick = L.tile_brick.as<int32_t>();
+        C.wb_ptr = L.wb_ptr.as<int32_t>();
+        C.wb = L.wb.as<float>();
+        C.soff = L.soff.as<uint16_t>();
+        C.fl = L.fl.as<uint16_t>();
+        C.val = L.val.as<__nv_bfloat16>();
+        C.wb_live = L.wb_live.as<uint8_t>();
+        C.c_soff = L.c_soff.as<uint16_t>();
+        C.c_fl = L.c_fl.as<uint16_t>();
+        C.c_val = L.c_val.as<__nv_bfloat16>();
+        C.c_chunk_end = L.c_chunk_end.as<int32_t>();
+        C.ctl = ctl;
+        C.n_sub = L.n_sub;
+        C.n_c = L.kp / DKC;
+        C.n_chunks = L.n_tiles * C.n_c;
+        C.wb_total = L.wb_total;
+        const unsigned cg = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((C.n_chunks + CMP_THREADS / 32 - 1) / (CMP_THREADS / 32), (int64_t)ix->num_sms * 16));
+        cmp_rebuild_kernel<<<cg, CMP_THREADS, 0, s>>>(C);
+        LIFE_CHECK_LAUNCH();
+    }
+    A.ctl = ctl;
+    A.want_mode = DSC_MODE_FULL;
     dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();
-    if (n_partial) *n_partial = grid;
+    A.want_mode = DSC_MODE_COMPACT;
+    A.soff = L.c_soff.as<uint16_t>();
+    A.fl = L.c_fl.as<uint16_t>();
+    A.val = L.c_val.as<__nv_bfloat16>();
+    A.chunk_end = L.c_chunk_end.as<int32_t>();
+    dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+    LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
 
@@ -1701,6 +2008,32 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
     wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();
+    return LIFE_OK;
+}
+
+life_status sparse_stats(life_index_s* ix, int64_t* out, cudaStream_t s) {
+    for (int i = 0; i < 6; ++i) out[i] = 0;
+    TileLayout& L = ix->tile;
+    if (!L.built || !L.sparse) return LIFE_OK;
+    SparseCtl c{};
+    const int n_c = L.kp / DKC;
+    std::vector<int32_t> ends((size_t)(L.n_tiles * n_c)), sp((size_t)(L.n_tiles * L.n_sub + 1));
+    LIFE_CUDA_TRY(cudaMemcpyAsync(&c, L.sparse_ctl.p, sizeof(SparseCtl), cudaMemcpyDeviceToHost, s));
+    if (!ends.empty()) {
+        LIFE_CUDA_TRY(cudaMemcpyAsync(ends.data(), L.c_chunk_end.p, sizeof(int32_t) * ends.size(),
+                                      cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.sub_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
+    }
+    LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t ncmp = 0;
+    for (int64_t t = 0; t < L.n_tiles; ++t)
+        for (int c2 = 0; c2 < n_c; ++c2) ncmp += ends[t * n_c + c2] - sp[t * L.n_sub + c2 * (DKC / SUB)];
+    out[0] = (int64_t)c.n_calls;
+    out[1] = (int64_t)c.n_compact_calls;
+    out[2] = (int64_t)c.n_compactions;
+    out[3] = c.have ? ncmp : 0;
+    out[4] = L.n_nnz;
+    out[5] = (int64_t)c.n_live_cmp;
     return LIFE_OK;
 }
 
