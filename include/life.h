@@ -294,6 +294,59 @@ LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const fl
                                int64_t max_iter, double tol, int32_t eq7_on_even, life_sbb_state* st,
                                void* workspace, void* stream);
 
+/* --------------------------------------------------- voxel-sharded SBB-NNLS */
+
+/*
+ * Index over the voxel range [v_begin, v_end) of a problem, for a solve sharded
+ * by voxels across workers (the distributed LiFE of the paper's related work,
+ * MPI-LiFE: rows of M are split over processes and the fascicle vectors are
+ * summed across them).  The shard keeps every fascicle (Nf is unchanged) and
+ * only the Phi entries of its voxels, renumbered v - v_begin, so its DSC gives
+ * rows v_begin..v_end-1 of y = M w and its WC gives one shard's share of
+ * g = M^T r (the shares sum to g).
+ *  atom, voxel, fasc, val   device, the whole problem's nnz entries
+ *  n_voxels                 voxels of the whole problem
+ *  voxel_ijk                optional device int32 [n_voxels·3] of the whole problem
+ *  opts, stream, out        as for life_build_index
+ * Synchronizes `stream`; allocates temporary device memory.
+ * Errors: LIFE_EINVAL for a range outside [0, n_voxels) or an empty range, and
+ * the errors of life_build_index for the shard's entries.
+ */
+LIFE_API life_status life_build_index_shard(const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
+                                            const float* val, int64_t nnz, int32_t n_theta, int32_t n_atoms,
+                                            int32_t n_voxels, int32_t n_fasc, const int32_t* voxel_ijk,
+                                            int32_t v_begin, int32_t v_end, const life_opts* opts, void* stream,
+                                            life_index* out);
+
+/*
+ * One phase of an SBB-NNLS iteration (Eq. 5-8, Algorithm 1) on one voxel shard.
+ * With M = [M_0; M_1; ...] split by voxels, M w and M g~ split by rows, while
+ * M^T e, M^T M g~, <e,e> and <M g~, M g~> are sums over shards; w, g~ and the
+ * state are the same on every shard.  An iteration is
+ *   phase 1:  e_s = M_s w - b_s;  scal[0] = Σ e_s²;  g = M_s^T e_s
+ *   exchange: g and scal[0] summed over all shards (every shard gets the sums)
+ *   phase 2:  g~ (the subspace projection), <g~,g~>, the stop test and the rule
+ *             of this iteration; v'_s = M_s g~;  scal[1] = Σ v'_s²;
+ *             u = M_s^T v'_s on Eq. 8 iterations (u = 0 on Eq. 7 iterations)
+ *   exchange: u and scal[1] summed over all shards
+ *   phase 3:  <u,u>, the step size (Eq. 7 or Eq. 8), w = [w - alpha g~]_+
+ * After phase 3 every shard holds the same w and state as an unsharded step,
+ * up to the summation order of the exchanged sums.  The library does not
+ * exchange: the caller sums g, u and scal between the phases (an all-reduce
+ * across processes, or a sum over shards held by one process).
+ *  b      float32 [Nθ·Nv_shard]: the shard's rows of the signal
+ *  w      float32 [Nf] (updated in phase 3); st device state (replicated)
+ *  g, u   float32 [Nf] device exchange buffers, owned by the caller
+ *  scal   double [2] device exchange scalars, owned by the caller
+ *  workspace  as for life_sbbnnls_step (life_sbb_workspace_bytes of this shard)
+ * A converged state makes phases 2 and 3 no-ops; phase 1 then leaves g = 0.
+ * Errors: LIFE_EINVAL for a null argument, an unaligned workspace or a phase
+ * other than 1, 2 or 3.
+ */
+LIFE_API life_status life_sbb_shard_phase(life_index idx, const float* D, const float* b, float* w, float* g,
+                                          float* u, double* scal, life_sbb_state* st, void* workspace, double tol,
+                                          int32_t eq7_on_even, int32_t phase, void* stream);
+
 /* --------------------------------------------------- connectome evaluation */
 
 /*

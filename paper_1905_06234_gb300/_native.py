@@ -29,7 +29,8 @@ EXPORTS = [
     "life_sbbnnls_step", "life_sbbnnls_solve", "life_batch_create", "life_batch_free", "life_batch_get_info",
     "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
     "life_index_autotune", "life_selftest_bounded_wait", "life_check_device_status", "life_last_error",
-    "life_version", "life_prune", "life_voxel_rmse", "life_index_sparse_stats",
+    "life_version", "life_prune", "life_voxel_rmse", "life_index_sparse_stats", "life_build_index_shard",
+    "life_sbb_shard_phase",
 ]
 
 
@@ -117,6 +118,9 @@ def load(build_if_missing: bool = False):
     L.life_selftest_bounded_wait.argtypes = [i64, P]
     L.life_check_device_status.argtypes = [P]
     L.life_index_sparse_stats.argtypes = [P, P, P]
+    L.life_build_index_shard.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, P, i32, i32,
+                                         ctypes.POINTER(life_opts), P, ctypes.POINTER(P)]
+    L.life_sbb_shard_phase.argtypes = [P, P, P, P, P, P, P, P, P, dbl, i32, i32, P]
     L.life_prune.argtypes = [i32, P, ctypes.c_float, P, P, P, P, P]
     L.life_voxel_rmse.argtypes = [i32, i32, P, P, P, P]
     L.life_last_error.restype = ctypes.c_char_p
@@ -540,3 +544,33 @@ def evaluate_connectome(index: LifeIndex, D, w, b, threshold=0.0):
     n = index.n_theta * index.n_voxels
     return dict(keep=keep, kept=kept, w_pruned=w_pruned, e=e, rmse=rmse,
                 global_rmse=float((ss / max(n, 1)).sqrt().item()))
+
+
+# ------------------------------------------------------- voxel-sharded solve
+
+def life_build_index_shard(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc, v_begin, v_end,
+                           voxel_ijk=None, precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0) -> LifeIndex:
+    """Index over voxels [v_begin, v_end) of a problem given as device COO arrays."""
+    L = load()
+    n = int(atom.numel())
+    for t, dt, nm in ((atom, torch.int32, "atom"), (voxel, torch.int32, "voxel"), (fasc, torch.int32, "fasc"),
+                      (val, torch.float32, "val")):
+        _need(t, dt, n, nm)
+    if voxel_ijk is not None:
+        _need(voxel_ijk, torch.int32, 3 * n_voxels, "voxel_ijk")
+    opts = life_opts(precision=int(precision), algo=int(algo), brick_dim=int(brick_dim))
+    h = ctypes.c_void_p()
+    _check(L.life_build_index_shard(_ptr(atom), _ptr(voxel), _ptr(fasc), _ptr(val), n, int(n_theta), int(n_atoms),
+                                    int(n_voxels), int(n_fasc), _ptr(voxel_ijk), int(v_begin), int(v_end),
+                                    ctypes.byref(opts), _stream(), ctypes.byref(h)))
+    return LifeIndex(h, L)
+
+
+def life_sbb_shard_phase(index: LifeIndex, D, b, w, g, u, scal, st, workspace, phase, tol=0.0, eq7_on_even=True):
+    """Phase 1, 2 or 3 of a sharded SBB-NNLS iteration (see include/life.h)."""
+    _need(g, torch.float32, index.n_fasc, "g")
+    _need(u, torch.float32, index.n_fasc, "u")
+    _need(scal, torch.float64, 2, "scal")
+    _check(load().life_sbb_shard_phase(index.handle, _ptr(D), _ptr(b), _ptr(w), _ptr(g), _ptr(u), _ptr(scal),
+                                       _ptr(st), _aligned(workspace), float(tol), 1 if eq7_on_even else 0, int(phase),
+                                       _stream()))

@@ -329,6 +329,49 @@ life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, f
     return LIFE_OK;
 }
 
+// One iteration of a voxel-sharded solve, in three phases around the two
+// exchanges of the Nf-vectors.  Shard s holds the rows of M for its voxels
+// (M = [M_0; M_1; ...]), so M w, the residual and M g~ split by rows, while
+// M^T e = Σ_s M_s^T e_s and M^T M g~ = Σ_s M_s^T (M_s g~) are sums over shards, as
+// are <e,e> and <Mg~,Mg~>.  w, g~ and the state are replicated: once g and u are
+// summed, every shard computes the same projection, step and update.
+//   phase 1: e_s = M_s w − b_s, scal[0] = Σ e_s², g = M_s^T e_s
+//            (caller: g and scal[0] summed over shards)
+//   phase 2: g~, <g~,g~>, stop test and rule; v'_s = M_s g~, scal[1] = Σ v'_s²,
+//            u = M_s^T v'_s on Eq. 8 iterations (else u = 0)
+//            (caller: u and scal[1] summed over shards)
+//   phase 3: <u,u>, the step size, w = [w − alpha g~]_+
+life_status sbb_enqueue_shard_phase(life_index_s* ix, const float* D, const float* b, float* w, float* g, float* u,
+                                    double* scal, life_sbb_state* st, void* workspace, double tol, int eq7_on_even,
+                                    int phase, cudaStream_t s) {
+    SbbWork W = carve(ix, workspace);
+    const int64_t nf = ix->nf;
+    const int vgrid = std::min(device_sm_count() * 4, RED_SLOTS);
+    if (phase == 1) {
+        int ne = 0;
+        LIFE_TRY(spmv_dsc(ix, D, w, b, W.e, W.pe, &ne, st, GATE_ACTIVE, s));
+        LIFE_TRY(reduce_partials(W.pe, ne, scal, s));
+        LIFE_TRY(spmv_wc(ix, D, W.e, g, st, GATE_ACTIVE, s, BatchGate(), true));
+    } else if (phase == 2) {
+        int nv_ = 0;
+        sbb_project_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, g, W.gt, nf, W.pg, st);
+        LIFE_CHECK_LAUNCH();
+        sbb_scalars1_kernel<<<1, RED_THREADS, 0, s>>>(st, scal, 1, W.pg, vgrid, tol, eq7_on_even);
+        LIFE_CHECK_LAUNCH();
+        LIFE_TRY(spmv_dsc(ix, D, W.gt, nullptr, W.e, W.pv, &nv_, st, GATE_ACTIVE_Y_EQ8, s));
+        LIFE_TRY(reduce_partials(W.pv, nv_, scal + 1, s));
+        LIFE_TRY(spmv_wc(ix, D, W.e, u, st, GATE_EQ8, s, BatchGate(), true));
+    } else {
+        int nu = 0;
+        LIFE_TRY(sumsq_f32(u, nf, W.pu, &nu, st, GATE_EQ8, s));
+        sbb_scalars2_kernel<<<1, RED_THREADS, 0, s>>>(st, scal + 1, 1, W.pu, nu);
+        LIFE_CHECK_LAUNCH();
+        sbb_update_kernel<<<vgrid, RED_THREADS, 0, s>>>(w, W.gt, nf, st);
+        LIFE_CHECK_LAUNCH();
+    }
+    return LIFE_OK;
+}
+
 }  // namespace life
 
 // ------------------------------------------------------ batched SBB-NNLS

@@ -1,0 +1,135 @@
+"""Voxel-sharded LiFE on one GPU, through the C ABI: shard indices over voxel
+ranges, and the sharded SBB-NNLS iteration with the shards' exchanges summed in
+process (the single-GPU stand-in for one shard per rank).
+
+Checks: each shard's DSC gives its rows of y = M w and the shards' WCs sum to
+g = M^T r (against the FP64 oracle, 1e-5 FP32 / 3e-3 BF16); sharded iterations
+agree with the oracle's iteration taken from the same w and state
+(teacher-forced, as for the unsharded solve), keep w and the state identical on
+every shard, and track the unsharded GPU solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1905_06234_gb300.shard import GpuPhases, LocalSum, ShardedSBB, gpu_shard, voxel_ranges
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def life():
+    import paper_1905_06234_gb300 as L
+    L.load(build_if_missing=True)
+    return L
+
+
+@pytest.fixture(scope="module")
+def case():
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    b = oracle.problem_signal(phi, D32, p.w_true, p.noise, p.n_theta, p.n_voxels)
+    return p, D32, phi, b
+
+
+PATHS = {"fp32": (0, 1, 1e-5), "bf16": (1, 2, 3e-3)}   # precision, algo, tolerance
+
+
+def shard_indices(life, p, ranges, precision, algo):
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).cuda().to(dt)
+    a, v, f = (dev(x, torch.int32) for x in (p.coo_atom, p.coo_voxel, p.coo_fasc))
+    x = dev(p.coo_val, torch.float32)
+    ijk = dev(np.asarray(p.voxel_ijk).reshape(-1), torch.int32)
+    return [life.life_build_index_shard(a, v, f, x, p.n_theta, p.n_atoms, p.n_voxels, p.n_fasc, v0, v1,
+                                        voxel_ijk=ijk, precision=precision, algo=algo) for v0, v1 in ranges]
+
+
+@pytest.mark.parametrize("path", ["fp32", "bf16"])
+def test_shard_spmv(life, case, path):
+    p, D32, phi, b = case
+    prec, algo, tol = PATHS[path]
+    nt, nf = p.n_theta, p.n_fasc
+    ranges = voxel_ranges(p.n_voxels, 3)
+    idxs = shard_indices(life, p, ranges, prec, algo)
+    counts = [int(((phi.voxel >= v0) & (phi.voxel < v1)).sum()) for v0, v1 in ranges]
+    assert [ix.nnz for ix in idxs] == counts and sum(counts) == len(phi)
+    rng = np.random.default_rng(3)
+    w = rng.random(nf).astype(np.float32)
+    r = rng.standard_normal(nt * p.n_voxels).astype(np.float32)
+    D = torch.from_numpy(D32).cuda()
+    y = np.concatenate([life.life_dsc(ix, D, torch.from_numpy(w).cuda())[0].cpu().numpy() for ix in idxs])
+    g = sum(life.life_wc(ix, D, torch.from_numpy(r[v0 * nt:v1 * nt]).cuda())[0].cpu().numpy().astype(np.float64)
+            for ix, (v0, v1) in zip(idxs, ranges))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    assert rel(y, oracle.dsc(phi, D32, w, nt, p.n_voxels)) <= tol
+    assert rel(g, oracle.wc(phi, D32, r, nt, nf)) <= tol
+
+
+@pytest.mark.parametrize("path,n_shards", [("fp32", 2), ("fp32", 3), ("bf16", 2)])
+def test_sharded_sbb_teacher_forced(life, case, path, n_shards):
+    p, D32, phi, b = case
+    prec, algo, _ = PATHS[path]
+    nt, nf = p.n_theta, p.n_fasc
+    ranges = voxel_ranges(p.n_voxels, n_shards)
+    idxs = shard_indices(life, p, ranges, prec, algo)
+    D = torch.from_numpy(D32).cuda()
+    shards = [gpu_shard(ix, D, torch.from_numpy(b[v0 * nt:v1 * nt]).cuda()) for ix, (v0, v1) in zip(idxs, ranges)]
+    solver = ShardedSBB(shards, GpuPhases(), LocalSum())
+    ost = oracle.SbbState()
+    worst = {}
+    # BF16: six iterations, as for the unsharded tensor-core path; later ones cancel
+    # the projected gradient so strongly that BF16 storage alone moves <g~,g~> by
+    # several per cent
+    for it in range(10 if path == "fp32" else 6):
+        w_in = shards[0].w.double().cpu().numpy().copy()
+        prev = life.read_sbb_state(shards[0].st)
+        ost.s.it, ost.s.alpha, ost.s.gg0 = prev["it"], prev["alpha"], prev["gg0"]
+        solver.step()
+        torch.cuda.synchronize()
+        oracle.sbb_step(phi, D32, b, w_in, nt, p.n_voxels, nf, ost)
+        sts = [life.read_sbb_state(s.st) for s in shards]
+        ws = [s.w.cpu().numpy() for s in shards]
+        for s_, w_ in zip(sts[1:], ws[1:]):   # replicated: identical on every shard
+            assert s_ == sts[0] and np.array_equal(w_, ws[0])
+        gst = sts[0]
+        assert gst["it"] == it + 1 and gst["eq"] == ost.eq
+        for k in ("obj", "gg", "vv", "uu", "alpha"):
+            ref = getattr(ost, k)
+            worst[k] = max(worst.get(k, 0.0), abs(gst[k] - ref) / max(abs(ref), 1e-300))
+        worst["w"] = max(worst.get("w", 0.0), rel(ws[0], w_in))
+    life.life_check_device_status()
+    print(path, n_shards, worst)
+    lim = 1e-4 if path == "fp32" else 3e-2
+    assert max(worst.values()) <= lim, worst
+
+
+def test_sharded_solve_tracks_unsharded(life, case):
+    p, D32, phi, b = case
+    nt = p.n_theta
+    D = torch.from_numpy(D32).cuda()
+    full = life.upload_problem(p)
+    w1 = torch.ones(p.n_fasc, device="cuda")
+    st1, ws1 = life.new_sbb_state(), life.new_sbb_workspace(full)
+    life.life_sbbnnls_solve(full, D, torch.from_numpy(b).cuda(), w1, 30, st1, ws1)
+    ranges = voxel_ranges(p.n_voxels, 2)
+    idxs = shard_indices(life, p, ranges, 0, 1)
+    shards = [gpu_shard(ix, D, torch.from_numpy(b[v0 * nt:v1 * nt]).cuda()) for ix, (v0, v1) in zip(idxs, ranges)]
+    ShardedSBB(shards, GpuPhases(), LocalSum()).solve(30)
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    s1, s2 = life.read_sbb_state(st1), life.read_sbb_state(shards[0].st)
+    assert s2["it"] == s1["it"] == 30
+    # the same arithmetic up to the summation order of the exchanged sums
+    assert rel(shards[0].w.cpu().numpy(), w1.cpu().numpy()) <= 1e-4
+    assert abs(s2["obj"] - s1["obj"]) <= 1e-4 * s1["obj"]
