@@ -62,7 +62,11 @@ typedef struct {
     int32_t sparse_dsc;    /* TC path: 1 = the index also keeps a live-entry DSC stream, and a DSC whose
                               input is sparse streams only the entries of fascicles with a non-zero input
                               (see life_dsc); 0 (default) = every DSC streams all entries */
-    int32_t reserved[2];   /* must be zero */
+    int32_t simt_kernels;  /* CUDA-core path, which kernels read the hybrid voxel-then-atom order one run
+                              of equal atoms at a time (one pass over D's column per run) rather than one
+                              entry at a time: 0 (default) = DSC by runs, WC by entries; 1 = both by
+                              entries; 2 = both by runs (life_index_autotune chooses per SpMV) */
+    int32_t reserved[1];   /* must be zero */
 } life_opts;
 
 typedef struct life_index_s* life_index;
@@ -81,7 +85,10 @@ typedef struct {
     int32_t brick_edge;    /* TC path: spatial brick edge in voxels (0 = runs of voxel ids, when no
                               coordinates were given) */
     int32_t wc_groups;     /* TC path: WC scatter groups the next WC launch uses */
-    int32_t tuned;         /* 1 if the autotuner chose brick_edge and wc_groups */
+    int32_t tuned;         /* 1 if the autotuner chose the layout parameters */
+    int32_t simt_runs;     /* CUDA-core kernels reading the hybrid order one atom run at a time:
+                              bit 0 = DSC, bit 1 = WC (otherwise one entry at a time) */
+    int32_t sparse_dsc;    /* TC path: 1 if the index keeps a live-entry DSC stream */
 } life_index_info;
 
 /*
@@ -463,9 +470,13 @@ LIFE_API life_status life_batch_solve(life_batch batch, const float* D, const fl
                                       void* workspace, void* stream);
 
 /*
- * Runs the autotuner on an existing index (TC path; a no-op otherwise): rebuilds
- * its tile layout with the brick edge and WC scatter groups that time fastest for
- * one SBB-NNLS iteration on this GPU.  Synchronizes `stream`.
+ * Runs the autotuner on an existing index.  TC path: rebuilds its tile layout
+ * with the brick edge and WC scatter groups that time fastest for one SBB-NNLS
+ * iteration on this GPU.  CUDA-core path: the runtime choice of restructuring
+ * (Sec. 4.1.2, hybrid data restructuring): DSC and WC are each timed three times
+ * reading the voxel-then-atom order entry by entry and run by run (one pass over
+ * D's column per run of equal atoms), and the faster is kept
+ * (info.simt_runs), for DSC and WC separately.  Synchronizes `stream`.
  */
 LIFE_API life_status life_index_autotune(life_index idx, void* stream);
 

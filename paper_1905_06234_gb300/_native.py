@@ -43,7 +43,7 @@ class LifeError(RuntimeError):
 class life_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("brick_dim", ctypes.c_int32),
                 ("wc_groups", ctypes.c_int32), ("autotune", ctypes.c_int32), ("sparse_dsc", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("simt_kernels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class life_index_info(ctypes.Structure):
@@ -52,7 +52,8 @@ class life_index_info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("algo", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
                 ("n_bricks", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("stream_bytes", ctypes.c_int64),
                 ("n_brick_fasc", ctypes.c_int64), ("n_sub", ctypes.c_int32), ("brick_edge", ctypes.c_int32),
-                ("wc_groups", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+                ("wc_groups", ctypes.c_int32), ("tuned", ctypes.c_int32), ("simt_runs", ctypes.c_int32),
+                ("sparse_dsc", ctypes.c_int32)]
 
 
 class life_batch_info(ctypes.Structure):
@@ -207,7 +208,7 @@ class LifeIndex:
 
 def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc, voxel_ijk=None,
                      precision=LIFE_FP32, algo=LIFE_ALGO_AUTO, brick_dim=0, wc_groups=0, autotune=False,
-                     sparse_dsc=False) -> LifeIndex:
+                     sparse_dsc=False, simt_kernels=0) -> LifeIndex:
     L = load()
     n = int(atom.numel())
     for t, dt, nm in ((atom, torch.int32, "atom"), (voxel, torch.int32, "voxel"), (fasc, torch.int32, "fasc"),
@@ -216,7 +217,8 @@ def life_build_index(atom, voxel, fasc, val, n_theta, n_atoms, n_voxels, n_fasc,
     if voxel_ijk is not None:
         _need(voxel_ijk, torch.int32, 3 * n_voxels, "voxel_ijk")
     opts = life_opts(precision=int(precision), algo=int(algo), brick_dim=int(brick_dim), wc_groups=int(wc_groups),
-                     autotune=1 if autotune else 0, sparse_dsc=1 if sparse_dsc else 0)
+                     autotune=1 if autotune else 0, sparse_dsc=1 if sparse_dsc else 0,
+                     simt_kernels=int(simt_kernels))
     h = ctypes.c_void_p()
     _check(L.life_build_index(_ptr(atom), _ptr(voxel), _ptr(fasc), _ptr(val), n, int(n_theta), int(n_atoms),
                               int(n_voxels), int(n_fasc), _ptr(voxel_ijk), ctypes.byref(opts), _stream(),

@@ -156,8 +156,42 @@ static life_status tune_wc(void* p) {
     return spmv_wc(c->ix, c->D, c->r, c->g, nullptr, GATE_NONE, c->s);
 }
 
+static life_status tune_dsc_simt(void* p) {
+    TuneCtx* c = static_cast<TuneCtx*>(p);
+    return dsc_simt(c->ix, c->D, c->w, nullptr, c->y, nullptr, nullptr, nullptr, GATE_NONE, c->s, BatchGate());
+}
+
+// CUDA-core path: the runtime choice of restructuring (Sec. 4.1.2 runs DSC and WC
+// three times per candidate and keeps the faster): the voxel order streamed entry
+// by entry, or the hybrid voxel-then-atom order with one D pass per atom run.
+static life_status autotune_simt(life_index_s* ix, cudaStream_t s) {
+    TmpBuf D, w, r, y, g;
+    const int64_t nd = (int64_t)ix->nt * ix->na, ny = (int64_t)ix->nt * ix->nv;
+    LIFE_TRY(D.alloc(sizeof(float) * nd, s));
+    LIFE_TRY(w.alloc(sizeof(float) * ix->nf, s));
+    LIFE_TRY(r.alloc(sizeof(float) * ny, s));
+    LIFE_TRY(y.alloc(sizeof(float) * ny, s));
+    LIFE_TRY(g.alloc(sizeof(float) * ix->nf, s));
+    fill_f32_kernel<<<256, 256, 0, s>>>(D.as<float>(), nd, 0.01f);
+    fill_f32_kernel<<<256, 256, 0, s>>>(w.as<float>(), ix->nf, 0.5f);
+    fill_f32_kernel<<<1024, 256, 0, s>>>(r.as<float>(), ny, 0.25f);
+    LIFE_CHECK_LAUNCH();
+    TuneCtx c{ix, D.as<float>(), w.as<float>(), r.as<float>(), y.as<float>(), g.as<float>(), s};
+    float t_dsc[2], t_wc[2];
+    for (int runs : {0, 1}) {
+        ix->simt_runs = runs ? (SIMT_RUNS_DSC | SIMT_RUNS_WC) : 0;
+        LIFE_TRY(time_ms(s, 3, &t_dsc[runs], tune_dsc_simt, &c));
+        LIFE_TRY(time_ms(s, 3, &t_wc[runs], tune_wc, &c));
+    }
+    ix->simt_runs = (t_dsc[1] < t_dsc[0] ? SIMT_RUNS_DSC : 0) | (t_wc[1] < t_wc[0] ? SIMT_RUNS_WC : 0);
+    LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    ix->tuned = 1;
+    return LIFE_OK;
+}
+
 life_status autotune_tc(life_index_s* ix, cudaStream_t s) {
-    if (!(ix->algo == LIFE_ALGO_TC && ix->tile.built)) return LIFE_OK;  // nothing to tune on CUDA cores
+    if (ix->algo == LIFE_ALGO_SIMT) return autotune_simt(ix, s);
+    if (!(ix->algo == LIFE_ALGO_TC && ix->tile.built)) return LIFE_OK;
     const TuneKey key{ilog2(ix->nnz), ilog2(ix->nv), ilog2(ix->nf), ix->nt, ix->na, ix->batch.n,
                       ix->voxel_ijk.p ? 1 : 0};
     int bestB = -1, bestG = 0;
@@ -252,7 +286,7 @@ extern "C" life_status life_batch_create(int32_t n, const life_index* idx, const
     }
     life_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 1; ++i)
         if (o.reserved[i] != 0) {
             set_error("life_batch_create: reserved option fields must be zero");
             return LIFE_EINVAL;

@@ -151,7 +151,7 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
         set_error("life_build_index: sparse_dsc must be 0 or 1");
         return LIFE_EINVAL;
     }
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 1; ++i)
         if (o.reserved[i] != 0) {
             set_error("life_build_index: reserved option fields must be zero");
             return LIFE_EINVAL;
@@ -187,6 +187,12 @@ extern "C" life_status life_build_index(const int32_t* atom, const int32_t* voxe
     ix->brick_dim = o.brick_dim > 0 ? o.brick_dim : 8;
     ix->wc_groups = o.wc_groups;
     ix->sparse_dsc = o.sparse_dsc;
+    if (o.simt_kernels < 0 || o.simt_kernels > 2) {
+        delete ix;
+        set_error("life_build_index: simt_kernels must be 0, 1 or 2");
+        return LIFE_EINVAL;
+    }
+    ix->simt_runs = o.simt_kernels == 0 ? SIMT_RUNS_DSC : (o.simt_kernels == 1 ? 0 : SIMT_RUNS_DSC | SIMT_RUNS_WC);
     life_status st = build_index_layouts(ix, atom, voxel, fasc, val, voxel_ijk, o.algo, s);
     if (st == LIFE_OK && o.autotune) st = autotune_tc(ix, s);
     if (st != LIFE_OK) {
@@ -220,6 +226,8 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
     I.precision = idx->precision;
     I.algo = idx->algo;
     I.tuned = idx->tuned;
+    I.simt_runs = idx->simt_runs;
+    I.sparse_dsc = idx->tile.sparse ? 1 : 0;
     I.n_tiles = idx->tile.n_tiles;
     I.n_bricks = idx->tile.n_bricks;
     const DevBuf* bufs[] = {&idx->ukey, &idx->uval, &idx->voxel_ijk, &idx->vox.vox_ptr, &idx->vox.atom,

@@ -98,6 +98,7 @@ struct TmpBuf {
 
 // ------------------------------------------------------------------ layouts
 
+enum : int32_t { SIMT_RUNS_DSC = 1, SIMT_RUNS_WC = 2 };
 constexpr int TILE_V = 128;        // voxels per tensor-core tile (MMA M)
 constexpr int MAX_BRICK_FASC = 15872;  // brick-local fascicle table capacity (62 KB of FP32)
 constexpr int RED_SLOTS = 4096;    // per-call FP64 partial-sum slots
@@ -209,6 +210,7 @@ struct life_index_s {
     int32_t precision = LIFE_FP32, algo = LIFE_ALGO_SIMT, brick_dim = 8;
     int32_t wc_groups = 0;      // TC WC scatter groups (0 = the largest that fits)
     int32_t sparse_dsc = 0;     // TC: keep a live-entry DSC stream (sparse-w-aware DSC)
+    int32_t simt_runs = 1;      // CUDA-core kernels by atom runs of the hybrid order: SIMT_RUNS_* bits
     int32_t tuned = 0;          // 1 once the autotuner chose brick_dim and wc_groups
     int32_t key_bits_v = 0, key_bits_a = 0, key_bits_f = 0;
     int device = 0;

@@ -7,6 +7,14 @@
 // skipped (Sec. 4.2.1, "BLAS call for DSC").  WC reduces each warp's 32 dot
 // products with a transpose-reduction of shuffles and adds val·dot into g[f]
 // with one atomic per nonzero (the paper's coefficient-based WC also uses atomics).
+//
+// Hybrid restructuring (Sec. 4.1.2: the voxel-restructured Phi with each voxel's
+// entries reordered by atom) is what the voxel layout stores, (v, a, f); the
+// RUNS variants use it: a run of equal atoms inside a voxel costs one pass over
+// D's column (DSC: D[:,a]·Σ val·w; WC: one dot <D[:,a], r[:,v]> shared by the
+// run's entries) instead of one per entry.  Which variant runs is chosen at
+// build time or, as the paper chooses its restructuring, by timing both
+// (life_index_autotune).
 #include "life_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -49,7 +57,7 @@ __device__ __forceinline__ float ldval<__nv_bfloat16>(const __nv_bfloat16* p, in
 }
 
 // y[:,v] = Σ_k D[:,a_k] val_k w[f_k]  (− b[:,v]);  per-block FP64 Σ out².
-template <int NTW, bool SMEM_D, class VT>
+template <int NTW, bool SMEM_D, class VT, bool RUNS>
 __global__ void __launch_bounds__(SIMT_THREADS)
 dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
                 const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D,
@@ -109,6 +117,33 @@ dsc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict_
             if (k < end) {
                 a_l = atom[k];
                 s_l = ldval<VT>(val, k) * __ldg(w + fasc[k]);
+            }
+            if (RUNS) {
+                // Hybrid order: inside a voxel the entries are sorted by atom, so a run
+                // of equal atoms is summed first (segmented scan over the lanes) and D's
+                // column is applied once per run: y[:,v] += D[:,a] · Σ_run val·w.
+                if (k >= end) a_l = -1 - lane;   // padding lanes form runs of their own
+                const int a_up = __shfl_up_sync(0xffffffffu, a_l, 1);
+                const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || a_up != a_l);
+                const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+                float rs = s_l;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float y2 = __shfl_up_sync(0xffffffffu, rs, o);
+                    if (lane - o >= start) rs += y2;
+                }
+                const int a_dn = __shfl_down_sync(0xffffffffu, a_l, 1);
+                uint32_t m = __ballot_sync(0xffffffffu, k < end && (lane == 31 || a_dn != a_l) && rs != 0.0f);
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float s = __shfl_sync(0xffffffffu, rs, j);
+                    const int a = __shfl_sync(0xffffffffu, a_l, j);
+                    const float* d = Ds + a * NTP + lane;
+#pragma unroll
+                    for (int q = 0; q < NTW; ++q) acc[q] = fmaf(d[q * 32], s, acc[q]);
+                }
+                continue;
             }
             const int cnt = min(32, end - base);
 #pragma unroll 4
@@ -171,7 +206,7 @@ __device__ __forceinline__ float transpose_reduce32(float (&x)[32], int lane) {
 }
 
 // g[f] += val_k <D[:,a_k], r[:,v_k]> for every nonzero (g zeroed by the caller).
-template <int NTW, bool SMEM_D, class VT>
+template <int NTW, bool SMEM_D, class VT, bool RUNS>
 __global__ void __launch_bounds__(SIMT_THREADS)
 wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__ atom,
                const int32_t* __restrict__ fasc, const VT* __restrict__ val, const float* __restrict__ D, int nt,
@@ -214,6 +249,35 @@ wc_simt_kernel(const int32_t* __restrict__ vox_ptr, const uint16_t* __restrict__
             const int k = base + lane;
             int a_l = 0;
             if (k < end) a_l = atom[k];
+            if (RUNS) {
+                // Hybrid order: one dot <D[:,a], r[:,v]> per run of equal atoms; run i's
+                // dot lands in lane i after the transpose reduction, and every entry of
+                // the run adds val·dot.
+                if (k >= end) a_l = -1 - lane;
+                const int a_dn = __shfl_down_sync(0xffffffffu, a_l, 1);
+                const uint32_t tails = __ballot_sync(0xffffffffu, k < end && (lane == 31 || a_dn != a_l));
+                const int nr = __popc(tails);
+                float part[32];
+                uint32_t m = tails;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float pj = 0.0f;
+                    if (j < nr) {
+                        const int jl = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int a = __shfl_sync(0xffffffffu, a_l, jl);
+                        const float* d = Ds + a * NTP + lane;
+#pragma unroll
+                        for (int q = 0; q < NTW; ++q) pj = fmaf(d[q * 32], rr[q], pj);
+                    }
+                    part[j] = pj;
+                }
+                const float dot_r = transpose_reduce32(part, lane);
+                const int ridx = __popc(tails & ((1u << lane) - 1u));
+                const float dot = __shfl_sync(0xffffffffu, dot_r, ridx & 31);
+                if (k < end) ptx::red_add_global_f32(g + fasc[k], ldval<VT>(val, k) * dot);
+                continue;
+            }
             float part[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -301,7 +365,8 @@ static life_status launch_dsc(life_index_s* ix, const float* D, const float* w, 
                               double* partial, int* n_partial, const life_sbb_state* gate, int gate_mode,
                               cudaStream_t s, const BatchGate& bg) {
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
-    auto kern = dsc_simt_kernel<NTW, SMEM, VT>;
+    // run-compressed kernels only with D in shared memory
+    auto kern = (SMEM && (ix->simt_runs & SIMT_RUNS_DSC)) ? dsc_simt_kernel<NTW, SMEM, VT, SMEM> : dsc_simt_kernel<NTW, SMEM, VT, false>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = ix->num_sms;
     kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
@@ -316,7 +381,7 @@ template <int NTW, bool SMEM, class VT>
 static life_status launch_wc(life_index_s* ix, const float* D, const float* r, float* g, const life_sbb_state* gate,
                              int gate_mode, cudaStream_t s, const BatchGate& bg) {
     const size_t smem = SMEM ? (size_t)ix->na * NTW * 32 * sizeof(float) : 0;
-    auto kern = wc_simt_kernel<NTW, SMEM, VT>;
+    auto kern = (SMEM && (ix->simt_runs & SIMT_RUNS_WC)) ? wc_simt_kernel<NTW, SMEM, VT, SMEM> : wc_simt_kernel<NTW, SMEM, VT, false>;
     if (SMEM) LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = ix->num_sms;
     kern<<<grid, SIMT_THREADS, smem, s>>>(ix->vox.vox_ptr.as<int32_t>(), ix->vox.atom.as<uint16_t>(),
