@@ -150,11 +150,11 @@ def workload_desc(p):
 class GpuPath:
     """Index + device buffers for one precision/algorithm choice."""
 
-    def __init__(self, life, p, D, b, precision, algo, autotune=False):
+    def __init__(self, life, p, D, b, precision, algo, autotune=False, sparse_dsc=False):
         import torch
         self.life = life
         t0 = time.time()
-        self.idx = life.upload_problem(p, precision=precision, algo=algo)
+        self.idx = life.upload_problem(p, precision=precision, algo=algo, sparse_dsc=sparse_dsc)
         if autotune:
             life.life_index_autotune(self.idx)
         torch.cuda.synchronize()
@@ -301,32 +301,127 @@ def job_throughput(steps, world, dt_max):
     return world * steps / dt_max
 
 
-def cpu_sample_baseline(p, D32, b, frac_voxels=0.15, reps=3):
-    """The FP64 oracle (single thread, as it stands) on a bounded sample: one SBB
-    iteration on the sub-problem of the first `frac_voxels` of the voxels."""
+def cpu_allcores_baseline(p, D32, b, reps=2):
+    """The FP64 baseline as it stands on all host cores (the oracle's arithmetic
+    with Phi grouped by voxel for DSC and by fascicle for WC, OpenMP), on the whole
+    workload: one untimed and `reps` timed SBB iterations from w = 1."""
     import numpy as np
     import oracle
-    nv_s = max(1, int(p.n_voxels * frac_voxels))
-    sel = p.coo_voxel < nv_s
-    phi = oracle.Phi(p.coo_atom[sel], p.coo_voxel[sel], p.coo_fasc[sel], p.coo_val[sel])
-    b_s = np.asarray(b[: p.n_theta * nv_s], np.float64)
-    best = None
+    t0 = time.perf_counter()
+    op = oracle.OmpProblem(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_voxels, p.n_fasc)
+    group_s = time.perf_counter() - t0
+    b64 = np.asarray(b, np.float64)
+    w = np.ones(p.n_fasc)
+    st = oracle.SbbState()
+    work = np.empty(2 * p.n_theta * p.n_voxels + 2 * p.n_fasc, np.float64)
+    op.sbb_step(D32, b64, w, st, work=work)
+    t0 = time.perf_counter()
     for _ in range(reps):
-        w = np.ones(p.n_fasc)
-        t0 = time.perf_counter()
-        oracle.sbb_step(phi, D32, b_s, w, p.n_theta, nv_s, p.n_fasc, oracle.SbbState())
-        dt = time.perf_counter() - t0
-        best = dt if best is None else min(best, dt)
-    frac_nnz = len(phi) / p.n_raw
-    return dict(iter_s=best, frac=frac_nnz, nnz_sample=len(phi), nv_sample=nv_s)
+        op.sbb_step(D32, b64, w, st, work=work)
+    dt = time.perf_counter() - t0
+    return dict(iter_s=dt / reps, reps=reps, cores=oracle.omp_threads(), group_s=group_s)
 
 
-def run_batched(life, D, max_iter=500, tol=1e-4):
+def full_solve(life, path, n_iter=500):
+    """The workload's full solve: n_iter SBB-NNLS iterations from w = 1 as one
+    graph launch (the graph is built by an untimed call first)."""
+    import torch
+    path.reset()
+    path.run_steps(1)
+    torch.cuda.synchronize()
+    path.reset()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    path.run_steps(n_iter)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    st = life.read_sbb_state(path.st)
+    out = {"iters": int(st["it"]), "s": t, "iter_per_s": st["it"] / t, "obj": st["obj"],
+           "rel_pg": (st["gg"] / st["gg0"]) ** 0.5 if st["gg0"] > 0 else None,
+           "zero_weights": float((path.w == 0).float().mean())}
+    if path.info.get("sparse_dsc"):
+        out["live_entry_stream"] = life.life_index_sparse_stats(path.idx)
+    return out
+
+
+def sparse_dsc_sweep(life, live, full, fracs=(0.0, 0.5, 0.9, 0.97), reps=10):
+    """DSC with the fused residual for weights with a given fraction of zeros: the
+    index with the live-entry stream (first call untimed: it builds the stream for
+    this support) against the same layout streaming every entry."""
+    import torch
+    p = live.p
+    y = torch.empty(p.n_theta * p.n_voxels, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    out = []
+    for zf in fracs:
+        w = torch.rand(p.n_fasc, device="cuda", generator=gen)
+        w[torch.rand(p.n_fasc, device="cuda", generator=gen) < zf] = 0.0
+        row = {"zero_frac": zf}
+        for name, path in (("live", live), ("full", full)):
+            row[name + "_ms"] = time_kernel(lambda: life.life_dsc(path.idx, path.D, w, b=path.b, y=y), reps) * 1e3
+        st = life.life_index_sparse_stats(live.idx)
+        row["live_entries"], row["entries"] = st["live_entries"], st["entries"]
+        out.append(row)
+    return out
+
+
+def time_to_tolerance(life, lo, hi, tol, tol_lo=1e-3, max_iter=500):
+    """Time to ‖g~‖ <= tol·‖g~_0‖ from w = 1: the plain path `hi` alone, the fast
+    path `lo` alone, and `lo` until tol_lo followed by `hi` to tol from the same w
+    and state (the state keeps ‖g~_0‖, so both phases test against the same
+    reference).  Graphs are built by untimed calls first."""
+    import torch
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def state(st):
+        x = life.read_sbb_state(st)
+        return {"iters": int(x["it"]), "converged": int(x["converged"]), "obj": x["obj"],
+                "rel_pg": (x["gg"] / x["gg0"]) ** 0.5 if x["gg0"] > 0 else None}
+
+    out = {"tol": tol, "tol_switch": tol_lo, "max_iter": max_iter}
+    for name, path in (("plain", hi), ("fast", lo)):
+        path.reset()
+        life.life_sbbnnls_solve(path.idx, path.D, path.b, path.w, 1, path.st, path.ws, tol=tol)
+        torch.cuda.synchronize()
+        path.reset()
+        t = timed(lambda: life.life_sbbnnls_solve(path.idx, path.D, path.b, path.w, max_iter, path.st, path.ws,
+                                                  tol=tol))
+        out[name] = dict(state(path.st), s=t)
+
+    def mixed():
+        life.life_sbbnnls_solve(lo.idx, lo.D, lo.b, lo.w, max_iter, lo.st, lo.ws, tol=tol_lo)
+        life.life_sbb_state_resume(lo.st)
+        life.life_sbbnnls_solve(hi.idx, hi.D, hi.b, lo.w, max_iter, lo.st, hi.ws, tol=tol)
+
+    lo.reset()
+    mixed()
+    torch.cuda.synchronize()
+    lo.reset()
+    t = timed(mixed)
+    out["fast_then_plain"] = dict(state(lo.st), s=t)
+    if out["plain"]["converged"] and out["fast_then_plain"]["converged"]:
+        out["speedup_at_tol"] = out["plain"]["s"] / t
+    return out
+
+
+def run_batched(life, D, max_iter=500, tol=1e-4, tol_switch=1e-3):
     """The batched workload: 16 independent problems of uneven size (Nf log-uniform
     in 1e4..2e5, cubic grids of edge 32..80, no mask) solved by SBB-NNLS to
     ‖g~‖/‖g~_0‖ <= tol, as one batched solve (one graph launch) and as 16
-    sequential plain solves, for the FP32 CUDA-core and BF16 tensor-core paths.
-    The BF16 batch's tile layout comes from the autotuner."""
+    sequential plain solves, for the FP32 CUDA-core and BF16 tensor-core paths,
+    and as BF16 batched iterations to tol_switch followed by FP32 batched
+    iterations to tol from the same weights and states.  The BF16 batch's tile
+    layout comes from the autotuner."""
     import torch
     import synth
     t0 = time.time()
@@ -338,9 +433,12 @@ def run_batched(life, D, max_iter=500, tol=1e-4):
            "max_iter": max_iter, "tol": tol, "gen_s": gen_s}
     bs = None
     s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batches, all_idxs = {}, []
     for name, prec, algo in (("fp32-simt", life.LIFE_FP32, life.LIFE_ALGO_SIMT),
                              ("bf16-tc", life.LIFE_BF16, life.LIFE_ALGO_TC)):
         idxs = [life.upload_problem(p, precision=prec, algo=algo) for p in probs]
+        all_idxs += idxs
         if bs is None:  # b_p = M_p w_true + noise from the FP32 DSC
             bs = []
             for p, ix in zip(probs, idxs):
@@ -350,6 +448,7 @@ def run_batched(life, D, max_iter=500, tol=1e-4):
         batch = life.life_batch_create(idxs, autotune=(algo == life.LIFE_ALGO_TC))
         torch.cuda.synchronize()
         create_s = time.time() - t0
+        batches[name] = batch
         ws = [torch.ones(p.n_fasc, device=dev) for p in probs]
         st = life.new_batch_states(len(probs))
         wsp = life.new_batch_workspace(batch)
@@ -358,7 +457,6 @@ def run_batched(life, D, max_iter=500, tol=1e-4):
         for w in ws:
             w.fill_(1.0)
         st.copy_(life.new_batch_states(len(probs)))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         life.life_batch_solve(batch, D, bs, ws, max_iter, st, wsp, tol=tol)
         e1.record(s)
@@ -390,10 +488,41 @@ def run_batched(life, D, max_iter=500, tol=1e-4):
                      "batched_iter_per_s": sum(its_b) / t_batch, "sequential_iter_per_s": sum(its_s) / t_seq,
                      "iters": its_b, "iters_sequential": its_s,
                      "converged": int(sum(x["converged"] for x in bst)),
+                     "final_obj": [x["obj"] for x in bst],
                      "max_rel_obj_diff_vs_sequential": obj_dev, "create_s": create_s, "batch": batch.info()}
-        batch.close()
-        for ix in idxs:
-            ix.close()
+        del seq
+    # BF16 batched iterations to tol_switch, then FP32 batched iterations to tol,
+    # from the same weights and states (both graphs built by an untimed run)
+    ws = [torch.ones(p.n_fasc, device=dev) for p in probs]
+    st = life.new_batch_states(len(probs))
+    wlo, whi = life.new_batch_workspace(batches["bf16-tc"]), life.new_batch_workspace(batches["fp32-simt"])
+
+    def mixed():
+        life.life_batch_solve(batches["bf16-tc"], D, bs, ws, max_iter, st, wlo, tol=tol_switch)
+        life.life_sbb_state_resume(st, len(probs))
+        life.life_batch_solve(batches["fp32-simt"], D, bs, ws, max_iter, st, whi, tol=tol)
+
+    mixed()
+    torch.cuda.synchronize()
+    for w in ws:
+        w.fill_(1.0)
+    st.copy_(life.new_batch_states(len(probs)))
+    e0.record(s)
+    mixed()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_mix = e0.elapsed_time(e1) / 1e3
+    mst = life.read_batch_states(st, len(probs))
+    out["bf16-tc+fp32-simt"] = {"batched_ms": t_mix * 1e3, "tol_switch": tol_switch,
+                                "iters": [int(x["it"]) for x in mst],
+                                "converged": int(sum(x["converged"] for x in mst)),
+                                "final_obj": [x["obj"] for x in mst],
+                                "speedup_vs_fp32_sequential": out["fp32-simt"]["sequential_ms"] / (t_mix * 1e3),
+                                "speedup_vs_fp32_batched": out["fp32-simt"]["batched_ms"] / (t_mix * 1e3)}
+    for b_ in batches.values():
+        b_.close()
+    for ix in all_idxs:
+        ix.close()
     return out
 
 
@@ -431,6 +560,11 @@ def run_ours(args):
             paths["bf16-tc"] = None
             if rank == 0:
                 print(f"# bf16 tensor-core path unavailable: {e}", file=sys.stderr)
+    live_path = None
+    if args.full_solve == "on" and paths.get("bf16-tc") is not None:
+        # the same tensor-core index with the live-entry DSC stream (sparse-w-aware DSC)
+        live_path = GpuPath(life, p, D, b, life.LIFE_BF16, life.LIFE_ALGO_TC, autotune=args.autotune,
+                            sparse_dsc=True)
     if args.profile:
         # Profiling mode: between cudaProfilerStart/Stop (for ncu
         # --profile-from-start off) run only the SBB steps of each path (one call
@@ -472,6 +606,14 @@ def run_ours(args):
     e2e_val, h2d, d2h = e2e_steps(life, path, e2e_n, 2)
     e2e_val = job_throughput(e2e_n, world, max_over_ranks(e2e_n / e2e_val, dist, dev))
     st = life.read_sbb_state(path.st)
+    solves, tol_run = None, None
+    if args.full_solve == "on":
+        solves = {k: full_solve(life, v) for k, v in paths.items() if v is not None}
+        if live_path is not None:
+            solves["bf16-tc-live"] = full_solve(life, live_path)
+            solves["bf16-tc-live"]["dsc_vs_zero_weights"] = sparse_dsc_sweep(life, live_path, paths["bf16-tc"])
+        if paths.get("bf16-tc") is not None:
+            tol_run = time_to_tolerance(life, paths["bf16-tc"], paths["fp32-simt"], tol=1e-4)
     batched = run_batched(life, D) if args.batched == "on" else None
     if rank != 0:
         if dist:
@@ -486,8 +628,8 @@ def run_ours(args):
     achieved = kern[f"{dom}_bytes"] / t_dom / 1e9
     peak = float(peaks.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"]))
     dsc_wc_gbs = (kern["dsc_bytes"] + kern["wc_bytes"]) / (kern["dsc_s"] + kern["wc_s"]) / 1e9
-    cpu = cpu_sample_baseline(p, D.cpu().numpy(), b.cpu().numpy())
-    cpu_value = cpu["frac"] / cpu["iter_s"]
+    cpu = cpu_allcores_baseline(p, D.cpu().numpy(), b.cpu().numpy())
+    cpu_value = 1.0 / cpu["iter_s"]
     value = job_throughput(args.steps, world, best["dt"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -509,14 +651,18 @@ def run_ours(args):
                       "wc_gbs": v["kern"]["wc_bytes"] / v["kern"]["wc_s"] / 1e9,
                       "index_build_s": v["path"].build_s} for k, v in results.items()},
         "vs_plain_fp32": (args.steps / best["dt"]) / (args.steps / results["fp32-simt"]["dt"]),
-        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "one FP64 SBB iteration on the voxels 0..%d sub-problem (%d of %d raw entries), "
-                                   "scaled by the entry fraction" % (cpu["nv_sample"], cpu["nnz_sample"], p.n_raw)},
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                         "sample": "%d FP64 SBB iterations of the whole workload (all %d raw entries) after one "
+                                   "untimed, on %d host threads (OpenMP: voxel-grouped DSC, fascicle-grouped WC); "
+                                   "grouping the entries took %.1f s" % (cpu["reps"], p.n_raw, cpu["cores"],
+                                                                         cpu["group_s"])},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_solve(path, args.steps) * world,
         "clocks": best["clocks"],
         "final_state": {"it": st["it"], "obj": st["obj"], "alpha": st["alpha"]},
         "tile_layout": {k: path.info[k] for k in ("brick_edge", "wc_groups", "tuned")},
+        "full_solve": solves,
+        "time_to_tolerance": tol_run,
         "batched": batched,
         "gen_s": gen_s,
     }
@@ -527,7 +673,9 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The FP64 oracle as it stands, on the host cores, each step a bounded sample."""
+    """The FP64 baseline as it stands on the host cores (the oracle's arithmetic,
+    OpenMP over voxel and fascicle groups): every step is one SBB iteration of the
+    whole workload, so ms_per_step x steps is the time that ran."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -536,29 +684,31 @@ def run_reference(args):
     p, _ = make_workload(args.workload)
     D64, _ = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)
     D32 = D64.astype(np.float32)
-    frac_v = 0.02
-    nv_s = max(1, int(p.n_voxels * frac_v))
-    sel = p.coo_voxel < nv_s
-    phi = oracle.Phi(p.coo_atom[sel], p.coo_voxel[sel], p.coo_fasc[sel], p.coo_val[sel])
-    b = oracle.problem_signal(phi, D32, p.w_true, p.noise[: p.n_theta * nv_s], p.n_theta, nv_s)
+    t0 = time.perf_counter()
+    op = oracle.OmpProblem(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_voxels, p.n_fasc)
+    group_s = time.perf_counter() - t0
+    b = (op.dsc(D32, p.w_true) + p.noise).astype(np.float32).astype(np.float64)
     w = np.ones(p.n_fasc)
     st = oracle.SbbState()
+    work = np.empty(2 * p.n_theta * p.n_voxels + 2 * p.n_fasc, np.float64)
     for _ in range(args.warmup):
-        oracle.sbb_step(phi, D32, b, w, p.n_theta, nv_s, p.n_fasc, st)
+        op.sbb_step(D32, b, w, st, work=work)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sbb_step(phi, D32, b, w, p.n_theta, nv_s, p.n_fasc, st)
+        op.sbb_step(D32, b, w, st, work=work)
     dt = time.perf_counter() - t0
-    frac = len(phi) / p.n_raw
-    value = frac * args.steps / dt
-    sample = ("FP64 SBB iterations on the voxels 0..%d sub-problem (%d of %d raw entries), "
-              "throughput scaled by the entry fraction" % (nv_s, len(phi), p.n_raw))
+    value = args.steps / dt
+    cores = oracle.omp_threads()
+    sample = ("whole workload (all %d raw entries), every step one FP64 SBB iteration on %d host threads "
+              "(OpenMP: voxel-grouped DSC, fascicle-grouped WC); grouping the entries took %.1f s"
+              % (p.n_raw, cores, group_s))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 / frac,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_desc(p), "path": "oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "final_state": {"it": st.it, "obj": st.obj}}
     print(json.dumps(line))
 
 
@@ -574,6 +724,9 @@ def main():
                     help="let the autotuner choose the BF16 tile layout of the main workload")
     ap.add_argument("--batched", default="on", choices=["on", "off"],
                     help="also time the batched workload (16 problems, batched vs sequential solves)")
+    ap.add_argument("--full-solve", dest="full_solve", default="on", choices=["on", "off"],
+                    help="also time the workload's full 500-iteration solve per path and the time to a "
+                         "1e-4 projected-gradient tolerance")
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + timed SBB steps inside cudaProfilerStart/Stop, print nothing")
     args = ap.parse_args()

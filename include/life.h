@@ -266,6 +266,16 @@ typedef struct {
     int32_t converged;   /* 1 once <g~,g~> = 0 or ‖g~‖ <= tol ‖g~_0‖ */
 } life_sbb_state;
 
+/*
+ * Clears the stop flag of n consecutive device states (st[0..n-1]) and keeps
+ * everything else: the iteration count, <g~_0, g~_0> and the last step size.  A
+ * solve that stopped at one tolerance then continues to a tighter one, also on
+ * another index of the same problem, e.g. full-precision iterations after
+ * reduced-precision ones, with the stopping test still relative to the first
+ * projected gradient.  Asynchronous.
+ */
+LIFE_API life_status life_sbb_state_resume(life_sbb_state* st, int32_t n, void* stream);
+
 /* Device bytes of the workspace one SBB call needs for this index. */
 LIFE_API life_status life_sbb_workspace_bytes(life_index idx, size_t* bytes);
 

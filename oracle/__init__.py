@@ -20,17 +20,23 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "oracle_omp.c")
+_OMP_LIB = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_omp = None
 
 ORDER_VOXEL, ORDER_FIBER, ORDER_ATOM = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (gcc, -O2, no FP contraction so both host ISAs round alike)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile liboracle.so (gcc, -O2, no FP contraction so both host ISAs round alike)
+    and liboracle_omp.so (the same arithmetic on all host cores, OpenMP)."""
+    for src, lib, extra in ((_SRC, _LIB, []), (_OMP_SRC, _OMP_LIB, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", *extra, "-o", tmp, src,
+                                   "-lm"])
+            os.replace(tmp, lib)
     return _LIB
 
 
@@ -217,3 +223,76 @@ def prune(w, threshold: float = 0.0):
     kept = np.empty(max(wf.size, 1), np.int32)
     n = _load().oracle_prune(wf.size, _p(wf), float(threshold), _p(keep), _p(kept))
     return keep, kept[:n].copy()
+
+
+# ------------------------------------------------------------ all host cores
+
+def _load_omp():
+    global _omp
+    if _omp is None:
+        build()
+        lib = ctypes.CDLL(_OMP_LIB)
+        P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.oracle_omp_threads.restype = i32
+        lib.oracle_omp_set_threads.argtypes = [i32]
+        lib.oracle_omp_group.argtypes = [i64, P, i64, P, P]
+        lib.oracle_omp_dsc.argtypes = [P, P, P, P, P, i32, P, P, i64, P]
+        lib.oracle_omp_wc.argtypes = [P, P, P, P, P, i32, P, P, i64, P]
+        lib.oracle_omp_sbb_step.argtypes = [P, P, P, P, P, P, P, P, i32, P, i64, i64, P, P, dbl, i32,
+                                            ctypes.POINTER(_SbbState), P]
+        _omp = lib
+    return _omp
+
+
+def omp_threads() -> int:
+    """Host threads the OpenMP baseline uses (OMP_NUM_THREADS, else all cores)."""
+    return int(_load_omp().oracle_omp_threads())
+
+
+def omp_set_threads(n: int):
+    """Threads for the following OpenMP baseline calls."""
+    _load_omp().oracle_omp_set_threads(int(n))
+
+
+class OmpProblem:
+    """Phi grouped by voxel (DSC) and by fascicle (WC) for the all-cores baseline.
+    Raw COO entries are accepted as they are: repeated (a, v, f) entries add up."""
+
+    def __init__(self, atom, voxel, fasc, val, n_theta, n_voxels, n_fasc):
+        L = _load_omp()
+        self.atom, self.voxel, self.fasc = _i32(atom), _i32(voxel), _i32(fasc)
+        self.val = _f64(val)
+        self.nt, self.nv, self.nf = int(n_theta), int(n_voxels), int(n_fasc)
+        n = self.atom.size
+        self.vptr = np.empty(self.nv + 1, np.int64)
+        self.vperm = np.empty(max(n, 1), np.int64)
+        self.fptr = np.empty(self.nf + 1, np.int64)
+        self.fperm = np.empty(max(n, 1), np.int64)
+        L.oracle_omp_group(n, _p(self.voxel), self.nv, _p(self.vptr), _p(self.vperm))
+        L.oracle_omp_group(n, _p(self.fasc), self.nf, _p(self.fptr), _p(self.fperm))
+
+    def dsc(self, D, x):
+        y = np.empty(self.nt * self.nv, np.float64)
+        Dd, xd = _f64(D), _f64(x)
+        _load_omp().oracle_omp_dsc(_p(self.vptr), _p(self.vperm), _p(self.atom), _p(self.fasc), _p(self.val),
+                                   self.nt, _p(Dd), _p(xd), self.nv, _p(y))
+        return y
+
+    def wc(self, D, r):
+        g = np.empty(self.nf, np.float64)
+        Dd, rd = _f64(D), _f64(r)
+        _load_omp().oracle_omp_wc(_p(self.fptr), _p(self.fperm), _p(self.atom), _p(self.voxel), _p(self.val),
+                                  self.nt, _p(Dd), _p(rd), self.nf, _p(g))
+        return g
+
+    def sbb_step(self, D, b, w, state: SbbState, tol=0.0, eq7_on_even=True, work=None):
+        """One SBB-NNLS iteration on all cores; updates ``w`` (float64) in place."""
+        assert w.dtype == np.float64 and w.flags.c_contiguous
+        if work is None:
+            work = np.empty(2 * self.nt * self.nv + 2 * self.nf, np.float64)
+        Dd, bd = _f64(D), _f64(b)
+        _load_omp().oracle_omp_sbb_step(_p(self.vptr), _p(self.vperm), _p(self.fptr), _p(self.fperm),
+                                        _p(self.atom), _p(self.voxel), _p(self.fasc), _p(self.val), self.nt, _p(Dd),
+                                        self.nv, self.nf, _p(bd), _p(w), float(tol), 1 if eq7_on_even else 0,
+                                        ctypes.byref(state.s), _p(work))
+        return state

@@ -12,7 +12,7 @@ from ._native import (  # noqa: F401
     new_sbb_workspace, read_sbb_state, LifeBatch, life_batch_create, life_batch_solve, life_index_autotune,
     new_batch_states, new_batch_workspace, read_batch_states, life_selftest_bounded_wait,
     life_prune, life_voxel_rmse, evaluate_connectome, life_index_sparse_stats,
-    life_build_index_shard, life_sbb_shard_phase,
+    life_build_index_shard, life_sbb_shard_phase, life_sbb_state_resume,
 )
 from .autograd import LifeDSC, LifeDictionary, dictionary, dsc  # noqa: F401
 from .problem import index_from_arrays, upload_problem  # noqa: F401

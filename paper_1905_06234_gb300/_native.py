@@ -30,7 +30,7 @@ EXPORTS = [
     "life_batch_offsets", "life_batch_index", "life_batch_workspace_bytes", "life_batch_solve",
     "life_index_autotune", "life_selftest_bounded_wait", "life_check_device_status", "life_last_error",
     "life_version", "life_prune", "life_voxel_rmse", "life_index_sparse_stats", "life_build_index_shard",
-    "life_sbb_shard_phase",
+    "life_sbb_shard_phase", "life_sbb_state_resume",
 ]
 
 
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = False):
     L.life_dot_f32.argtypes = [i64, P, P, P, P]
     L.life_sbb_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.life_sbb_state_init.argtypes = [P, P]
+    L.life_sbb_state_resume.argtypes = [P, i32, P]
     L.life_sbbnnls_step.argtypes = [P, P, P, P, P, P, dbl, i32, P]
     L.life_sbbnnls_solve.argtypes = [P, P, P, P, i64, dbl, i32, P, P, P]
     L.life_batch_create.argtypes = [i32, P, ctypes.POINTER(life_opts), P, ctypes.POINTER(P)]
@@ -355,6 +356,12 @@ def _aligned(ws):
 
 def life_sbb_state_init(st):
     _check(load().life_sbb_state_init(_ptr(st), _stream()))
+
+
+def life_sbb_state_resume(st, n: int = 1):
+    """Clears the stop flag of n device states (see include/life.h)."""
+    _need(st, torch.uint8, n * SBB_STATE_BYTES, "st")
+    _check(load().life_sbb_state_resume(_ptr(st), int(n), _stream()))
 
 
 def read_sbb_state(st) -> dict:

@@ -225,6 +225,26 @@ extern "C" life_status life_dot_f32(int64_t n, const float* x, const float* y, d
     return check_stream_ok("life_dot_f32");
 }
 
+namespace life {
+// Clears the stop flag of n states; the iteration count, ‖g~_0‖² and the last
+// step size are kept, so the iterations continue where they stopped.
+__global__ void sbb_resume_kernel(life_sbb_state* st, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        st[i].converged = 0;
+        st[i].eq = 0;
+    }
+}
+}  // namespace life
+
+extern "C" life_status life_sbb_state_resume(life_sbb_state* st, int32_t n, void* stream) {
+    if (!st || n < 1) {
+        set_error("life_sbb_state_resume: null state or n < 1");
+        return LIFE_EINVAL;
+    }
+    sbb_resume_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(st, n);
+    return check_stream_ok("life_sbb_state_resume");
+}
+
 extern "C" life_status life_sbb_state_init(life_sbb_state* st, void* stream) {
     if (!st) {
         set_error("life_sbb_state_init: null state");

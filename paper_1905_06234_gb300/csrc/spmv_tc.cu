@@ -149,13 +149,24 @@ struct SparseCtl {
     uint32_t compact_now;             // the current call rebuilds the compacted stream
     uint32_t have;                    // a compacted stream exists
     uint32_t gather_done;             // blocks of the gather finished (the last one decides)
+    uint32_t since;                   // decisions since the last rebuild
+    uint32_t gap;                     // decisions a rebuild for a stale live set must wait (backoff)
 };
 
 // Thresholds of the decision: the compacted stream is used only while the live
 // slots are at most DENSE_FRAC of all slots, and rebuilt once the live count has
-// fallen below SHRINK_FRAC of the count it was built for.
+// fallen below SHRINK_FRAC of the count it was built for.  A live set that went
+// stale may be rebuilt only `gap` decisions after the last rebuild, and each such
+// rebuild doubles the gap (up to MAX_GAP): when fascicles keep entering the
+// support (SBB-NNLS iterations bring zero weights back to life), the calls fall
+// back to the full stream instead of paying a rebuild every time.
 constexpr double DENSE_FRAC = 0.92;
 constexpr double SHRINK_FRAC = 0.9;
+constexpr uint32_t MAX_GAP = 256;
+// Who may rebuild: never (the SBB step's DSC of w), with the backoff (the SBB
+// step's DSC of the projected gradient), or whenever the live set is stale or
+// shrunk (public DSC calls).
+enum : int { ALLOW_NONE = 0, ALLOW_BACKOFF = 1, ALLOW_FREE = 2 };
 
 // The decision for this call, taken by the last block of the gather once every
 // block's counts are in.
@@ -172,14 +183,19 @@ __device__ void dsc_decide(SparseCtl* c, unsigned long long n_slots, int allow, 
         return;
     }
     uint32_t mode, cmp = 0u;
+    if (c->gap == 0u) c->gap = 1u;
+    c->since += 1u;
+    const bool shrunk = (double)nl < SHRINK_FRAC * (double)c->n_live_cmp;
     if ((double)nl > DENSE_FRAC * (double)n_slots) {
         mode = DSC_MODE_FULL;
-    } else if (allow && (!c->have || stale || (double)nl < SHRINK_FRAC * (double)c->n_live_cmp)) {
+    } else if (allow && (!c->have || (stale && (allow == ALLOW_FREE || c->since >= c->gap)) || (!stale && shrunk))) {
+        if (c->have && stale && allow == ALLOW_BACKOFF) c->gap = c->gap * 2u < MAX_GAP ? c->gap * 2u : MAX_GAP;
         cmp = 1u;
         mode = DSC_MODE_COMPACT;
         c->have = 1u;
         c->n_live_cmp = nl;
         c->n_compactions += 1ull;
+        c->since = 0u;
     } else {
         mode = stale ? DSC_MODE_FULL : DSC_MODE_COMPACT;
     }
@@ -1921,11 +1937,12 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
         if (sparse)
             // the last block decides: full or compacted stream, rebuild or not (the
             // SBB step's DSC of w never rebuilds: its support lies inside that of the
-            // previous projected gradient; every other call may)
+            // previous projected gradient; the DSC of the projected gradient rebuilds
+            // with the backoff; a public call whenever its input needs it)
             wb_gather_live_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(
                 L.wb_src.as<int32_t>(), L.wb_total, w, L.wb.as<float>(), L.wb_live.as<uint8_t>(),
                 L.sparse_ctl.as<SparseCtl>(), (unsigned long long)L.n_brick_slots,
-                (gate && gate_mode == GATE_ACTIVE) ? 0 : 1, gate, gate_mode);
+                !gate ? ALLOW_FREE : (gate_mode == GATE_ACTIVE ? ALLOW_NONE : ALLOW_BACKOFF), gate, gate_mode);
         else
             wb_gather_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(L.wb_src.as<int32_t>(), L.wb_total, w,
                                                                       L.wb.as<float>());

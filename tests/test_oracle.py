@@ -376,3 +376,40 @@ def test_prune_invariants():
     assert (np.diff(kept) > 0).all() and keep.sum() == kept.size
     assert (w[kept] > 0).all() and not (w[keep == 0] > 0).any()
     assert oracle.prune(np.zeros(0, np.float32))[1].size == 0
+
+
+# ------------------------------------------------------- all-cores baseline
+
+
+def test_omp_baseline_matches_serial_oracle():
+    """The all-cores FP64 baseline (Phi grouped by voxel and by fascicle)
+    reproduces the serial oracle's SpMVs and SBB iterations to FP64 rounding on the
+    merged Phi, and to the float32 rounding of the merged values on the raw list
+    with its repeated (a, v, f) entries."""
+    p = synth.make_problem("omp", seed=1905062351, n_theta=24, n_atoms=40, grid=(6, 6, 5), n_fasc=60,
+                           steps=(8, 20))
+    D, _ = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    assert len(phi) < len(p.coo_atom)  # the raw list repeats some (a, v, f)
+    op = oracle.OmpProblem(phi.atom, phi.voxel, phi.fasc, phi.val, p.n_theta, p.n_voxels, p.n_fasc)
+    raw = oracle.OmpProblem(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_voxels, p.n_fasc)
+    rng = np.random.default_rng(8)
+    w = rng.random(p.n_fasc)
+    r = rng.standard_normal(p.n_theta * p.n_voxels)
+    y_ref = oracle.dsc(phi, D, w, p.n_theta, p.n_voxels)
+    g_ref = oracle.wc(phi, D, r, p.n_theta, p.n_fasc)
+    np.testing.assert_allclose(op.dsc(D, w), y_ref, rtol=1e-12, atol=1e-12 * np.abs(y_ref).max())
+    np.testing.assert_allclose(op.wc(D, r), g_ref, rtol=1e-12, atol=1e-12 * np.abs(g_ref).max())
+    assert np.linalg.norm(raw.dsc(D, w) - y_ref) <= 1e-7 * np.linalg.norm(y_ref)
+    assert np.linalg.norm(raw.wc(D, r) - g_ref) <= 1e-7 * np.linalg.norm(g_ref)
+    b = oracle.problem_signal(phi, D, p.w_true, p.noise, p.n_theta, p.n_voxels)
+    w1, w2 = np.ones(p.n_fasc), np.ones(p.n_fasc)
+    s1, s2 = oracle.SbbState(), oracle.SbbState()
+    for _ in range(10):
+        oracle.sbb_step(phi, D, b, w1, p.n_theta, p.n_voxels, p.n_fasc, s1)
+        op.sbb_step(D, b, w2, s2)
+    assert s1.it == s2.it == 10 and s1.eq == s2.eq
+    for k in ("obj", "gg", "vv", "uu", "alpha"):
+        assert abs(getattr(s1, k) - getattr(s2, k)) <= 1e-9 * abs(getattr(s1, k))
+    np.testing.assert_allclose(w2, w1, rtol=1e-9, atol=1e-12)
+    assert oracle.omp_threads() >= 1
