@@ -30,18 +30,20 @@ UNIT = "iter/s"
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
-# DRAM bytes (read + write) of the launches of one timed tensor-core call on the
-# paper-scale workload, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, a one-pass metric set): DSC with the fused residual =
-# brick weight gather + DSC kernel; WC through the public call = per-tile max|r|
-# pass + WC kernel.  The figures hold only for the kernel source that was
-# captured; after any change to it the bench reports null.
+# DRAM bytes (read + write) of the launches of one timed tensor-core call, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric
+# set) on the paper-density workload at a third of the size: DSC with the fused
+# residual = brick weight gather + DSC kernel; WC through the public call =
+# per-tile max|r| pass + WC kernel.  Scaled to the timed workload by its entry
+# count (the traffic grows with the entries and voxels alike).  The figures hold
+# only for the kernel source that was captured; after any change to it the bench
+# reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "c420e01f5f716e8d0aaa18a0b97f4c9bd32046d8d3b8b35c0d410efd5b42b86e",
-    "nnz": 79521683,
-    "bytes": {"dsc": (38386176 + 29952) + (649297664 + 110706432),
-              "wc": (134849280 + 124416) + (687108864 + 5592832)},
+    "sha256": "5aa5bffd72b8b43d57bd15e54f1ab2d9c8486f6ddc42ac15e4cfa346b34a47ae",
+    "nnz": 23816750,
+    "bytes": {"dsc": (11036416 + 0) + (193704448 + 16558080),
+              "wc": (39992576 + 0) + (202005504 + 70656)},
 }
 
 
@@ -642,7 +644,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
                      "traffic": kernel_traffic(best_name, dom, path.info["nnz"]),
-                     "traffic_note": "ncu DRAM bytes of one launch of this kernel on this workload"},
+                     "traffic_note": "ncu DRAM bytes of one timed call of this kernel (its launches), captured on the "
+                                     "one-third-size paper-density case and scaled by the entry count"},
         "dsc_wc": {"gbs": dsc_wc_gbs, "frac_of_peak": dsc_wc_gbs / peak, "dsc_ms": kern["dsc_s"] * 1e3,
                    "wc_ms": kern["wc_s"] * 1e3},
         "paths": {k: {"iter_per_s": args.steps / v["dt"], "dsc_ms": v["kern"]["dsc_s"] * 1e3,
