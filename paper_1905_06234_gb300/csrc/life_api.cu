@@ -239,7 +239,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
                             &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->tile.wb_src,
                             &idx->tile.wb_ptr, &idx->tile.wb, &idx->tile.brick_cv, &idx->tile.tile_amax, &idx->red,
                             &idx->tile.c_soff, &idx->tile.c_fl, &idx->tile.c_val, &idx->tile.c_chunk_end,
-                            &idx->tile.wb_live, &idx->tile.sparse_ctl, &idx->tile.tile_brick};
+                            &idx->tile.wb_live, &idx->tile.sparse_ctl, &idx->tile.tile_brick, &idx->tile.x_amax};
     int64_t tot = 0;
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;

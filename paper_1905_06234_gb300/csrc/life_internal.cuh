@@ -169,6 +169,8 @@ struct TileLayout {
     DevBuf wb_live;          // uint8 [wb_total]: 1 for slots in the live set
     DevBuf sparse_ctl;       // device decision state of the compacted stream
     DevBuf tile_brick;       // int32 [n_tiles] brick of each tile
+    float run_vmax = 0.0f;   // largest Σ|val| (BF16 values) over one (atom, voxel) run of the DSC stream
+    DevBuf x_amax;           // uint32 [num_sms·8] bits of max |x| per block of a DSC's weight gather
     DevBuf brick_cv;         // float [n_bricks]: (largest entry count of a fascicle) x (largest |val|)
     DevBuf tile_amax;        // uint32 [n_tiles * 4]: bits of max |r| per tile row quarter (written by
                              // every DSC that stores y, and by WC calls whose r did not come from one)

@@ -13,6 +13,7 @@
 // accumulation in TMEM), one 128-voxel tile at a time (MMA M = 128).  Operands
 // are K-major, no-swizzle core-matrix layouts in shared memory.
 #include <algorithm>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -104,13 +105,34 @@ __device__ __forceinline__ float gather_slot(const float* __restrict__ w, int32_
     return id >= 0 ? __ldg(w + id) : 0.0f;
 }
 
+__device__ __forceinline__ uint32_t absmax4_bits(const float4& v) {
+    return max(max(__float_as_uint(v.x) & 0x7FFFFFFFu, __float_as_uint(v.y) & 0x7FFFFFFFu),
+               max(__float_as_uint(v.z) & 0x7FFFFFFFu, __float_as_uint(v.w) & 0x7FFFFFFFu));
+}
+
+// Block maximum of the bits of |x| (non-negative floats order as unsigned ints,
+// NaN above +inf), written by thread 0 to out[blockIdx.x].
+__device__ __forceinline__ void block_absmax_out(uint32_t m, uint32_t* out) {
+    __shared__ uint32_t wmax[32];
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0u;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = max(t, wmax[i]);
+        out[blockIdx.x] = t;
+    }
+}
+
 // wb[j] = w[wb_src[j]] (0 for padding slots): the DSC's brick weight tables for
-// this call's w.  (n is a multiple of 4 and both arrays are 16-byte aligned: each
-// thread moves 4 slots per step with one 16-byte load of indices, four
-// independent gathers and one 16-byte store.)
+// this call's w, and per block the bits of max |w| over the gathered slots (the
+// scale of the DSC's FP16 S operand).  (n is a multiple of 4 and both arrays are
+// 16-byte aligned: each thread moves 4 slots per step with one 16-byte load of
+// indices, four independent gathers and one 16-byte store.)
 __global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
-                                 float* __restrict__ wb) {
+                                 float* __restrict__ wb, uint32_t* __restrict__ amax) {
     const int64_t n4 = n >> 2;
+    uint32_t m = 0u;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
         const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
         float4 v;
@@ -119,7 +141,9 @@ __global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, co
         v.z = gather_slot(w, id.z);
         v.w = gather_slot(w, id.w);
         reinterpret_cast<float4*>(wb)[j] = v;
+        m = max(m, absmax4_bits(v));
     }
+    block_absmax_out(m, amax);
 }
 
 // ------------------------------------------------- live-entry DSC stream
@@ -216,12 +240,14 @@ __global__ void __launch_bounds__(GATHER_THREADS) wb_gather_live_kernel(const in
                                                                         const uint8_t* __restrict__ live,
                                                                         SparseCtl* __restrict__ ctl,
                                                                         unsigned long long n_slots, int allow,
-                                                                        const life_sbb_state* gate, int gate_mode) {
+                                                                        const life_sbb_state* gate, int gate_mode,
+                                                                        uint32_t* __restrict__ amax) {
     __shared__ unsigned int blk_n, blk_stale, last;
     if (threadIdx.x == 0) blk_n = blk_stale = 0u;
     __syncthreads();
     const int64_t n4 = n >> 2;
     unsigned int cnt = 0u, stale = 0u;
+    uint32_t am = 0u;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
         const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
         const uchar4 lv = __ldg(reinterpret_cast<const uchar4*>(live) + j);
@@ -231,6 +257,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) wb_gather_live_kernel(const in
         v.z = gather_slot(w, id.z);
         v.w = gather_slot(w, id.w);
         reinterpret_cast<float4*>(wb)[j] = v;
+        am = max(am, absmax4_bits(v));
         // padding slots hold 0 and never count
         const bool nx = v.x != 0.0f, ny = v.y != 0.0f, nz = v.z != 0.0f, nw = v.w != 0.0f;
         cnt += (unsigned)nx + (unsigned)ny + (unsigned)nz + (unsigned)nw;
@@ -244,7 +271,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) wb_gather_live_kernel(const in
         atomicAdd(&blk_n, cnt);
         atomicOr(&blk_stale, stale);
     }
-    __syncthreads();
+    block_absmax_out(am, amax);   // (its barrier also orders the block counts above)
     if (threadIdx.x == 0) {
         if (blk_n) atomicAdd(&ctl->n_live, (unsigned long long)blk_n);
         if (blk_stale) atomicOr(&ctl->stale, 1u);
@@ -467,6 +494,22 @@ __global__ void wc_stream_kernel(const uint64_t* __restrict__ key3, const uint32
 
 __global__ void fill_kernel(int32_t* p, int64_t n, int32_t v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Bits of the largest Σ|val| over the entries of one (atom, voxel) run of the DSC
+// stream (a run starts at an entry without the continuation flag): with max |x|
+// it bounds every S value of a DSC.
+__global__ void run_vmax_kernel(const uint16_t* __restrict__ fl, const __nv_bfloat16* __restrict__ val, int64_t m,
+                                uint32_t* __restrict__ out) {
+    uint32_t best = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        if (fl[j] & CONT) continue;
+        float sum = fabsf(__bfloat162float(val[j]));
+        for (int64_t k = j + 1; k < m && (fl[k] & CONT); ++k) sum += fabsf(__bfloat162float(val[k]));
+        best = max(best, __float_as_uint(sum));
+    }
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
 
 struct HostTiles {
@@ -723,6 +766,20 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.sub_ptr.as<int32_t>(), n_segs + 1, 0);
         LIFE_CHECK_LAUNCH();
     }
+    L.run_vmax = 0.0f;
+    if (m > 0) {
+        TmpBuf rv;
+        LIFE_TRY(rv.alloc(sizeof(uint32_t), s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(rv.p, 0, sizeof(uint32_t), s));
+        run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), m, rv.as<uint32_t>());
+        LIFE_CHECK_LAUNCH();
+        uint32_t bits = 0u;
+        LIFE_CUDA_TRY(cudaMemcpyAsync(&bits, rv.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+        std::memcpy(&L.run_vmax, &bits, sizeof(float));
+    }
+    LIFE_TRY(L.x_amax.alloc(sizeof(uint32_t) * (size_t)std::max(ix->num_sms, 1) * 8));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.x_amax.p, 0, sizeof(uint32_t) * (size_t)std::max(ix->num_sms, 1) * 8, s));
     // WC streams (row quarter major inside each tile)
     const int64_t n_wsegs = H.n_tiles * 4 * L.n_sub;
     LIFE_TRY(L.wkey.alloc(sizeof(uint16_t) * m_pad));
@@ -861,6 +918,9 @@ struct TcArgs {
     uint32_t* tile_amax;      // bits of max |r| per (tile, row quarter): written by DSC, read by WC
     const life_sbb_state* gate;
     int gate_mode;
+    const uint32_t* x_amax;    // DSC: bits of max |x| per block of this call's weight gather
+    int n_xamax;
+    float run_vmax;            // DSC: largest Σ|val| over the entries of one (atom, voxel) run
     const int32_t* chunk_end;  // DSC on the live-entry stream: end of each chunk's entries (else NULL:
                                // a chunk ends where the next begins)
     const SparseCtl* ctl;  // DSC: when set, the launch runs only if ctl->mode == want_mode
@@ -996,8 +1056,8 @@ __host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb) {
     return d + DSTAGE * DS_BYTES + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) + 1024;
 }
 
-__device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s) {
-    reinterpret_cast<__nv_bfloat16*>(S)[so] = __float2bfloat16_rn(s);
+__device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s, float ss) {
+    reinterpret_cast<__half*>(S)[so] = __float2half_rn(s * ss);
 }
 
 // S[a, row] for the runs that start inside this slot (a run = entries with the
@@ -1013,7 +1073,7 @@ struct RunState {
 
 template <bool CHECK>
 __device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, int end, const float* wl,
-                                         unsigned char* S, RunState& st) {
+                                         unsigned char* S, RunState& st, float ss) {
     // straight-line code: every lane does the same work for every entry
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
@@ -1025,7 +1085,7 @@ __device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, 
         const uint32_t f = u16_at(s.fl, e);
         const float t = in ? bf16_at(s.val, e) * wl[f & 0x7FFFu] : 0.0f;
         const bool head = in && !(f & CONT);
-        if (head && st.have) store_s(S, st.so, st.cs);   // the previous run ends here
+        if (head && st.have) store_s(S, st.so, st.cs, ss);   // the previous run ends here
         st.lead += (!st.have && !head) ? t : 0.0f;       // continuation of a run owned by the lane before
         st.cs = head ? t : st.cs + t;
         st.so = head ? u16_at(s.key, e) : st.so;
@@ -1035,10 +1095,10 @@ __device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, 
 }
 
 __device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, int base, int beg, int end,
-                                         const float* wl, unsigned char* S, int lane) {
+                                         const float* wl, unsigned char* S, int lane, float ss) {
     RunState st{false, false, 0u, 0.0f, 0.0f};
-    if (base >= beg && base + SLOT <= end) dsc_runs<false>(s, base, beg, end, wl, S, st);
-    else dsc_runs<true>(s, base, beg, end, wl, S, st);
+    if (base >= beg && base + SLOT <= end) dsc_runs<false>(s, base, beg, end, wl, S, st, ss);
+    else dsc_runs<true>(s, base, beg, end, wl, S, st, ss);
     // a run may pass through this whole slot into the one after it
     const int through = (!st.head_seen && base + SLOT < end) ? 1 : 0;
     const float nlead = __shfl_down_sync(0xffffffffu, st.lead, 1);
@@ -1056,7 +1116,7 @@ __device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, in
                 }
             }
         }
-        store_s(S, st.so, st.cs);
+        store_s(S, st.so, st.cs, ss);
     }
 }
 
@@ -1106,11 +1166,55 @@ __device__ __forceinline__ void stage_d(const TcArgs& A, unsigned char* dst, uin
     }
 }
 
+// ------------------------------------------------------ FP16 MMA operands
+// The stored precision stays BF16 (Phi values, D); the operands the tensor cores
+// read are FP16 (11 significand bits) under exact power-of-two scales, so that
+// the per-call roundings of S (DSC) and of the r tile (WC) cost 2^-11 instead
+// of the 2^-8 of BF16 (BF16 D values convert to FP16 exactly once scaled into
+// FP16's normal range).
+
+// Largest k with bound·2^k < 2^15 (FP16 holds up to 65504), for bound < 2^e;
+// 0 for a zero or non-finite bound (NaN and inf then propagate as such).
+__device__ __forceinline__ int f16_scale_exp(uint32_t bound_bits) {
+    const float b = __uint_as_float(bound_bits);
+    if (bound_bits == 0u || !(b <= 3.0e38f)) return 0;
+    int e = 0;
+    (void)frexpf(b, &e);
+    return max(-120, min(120, 15 - e));
+}
+
+// Bits of max |v| over n BF16 values at p (a multiple of 2).
+__device__ __forceinline__ uint32_t bf16_absmax_bits(const unsigned char* p, uint32_t n, int tid, int nthr) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+    uint32_t m = 0u;
+    for (uint32_t i = tid; i < n / 2; i += nthr) {
+        const uint32_t u = q[i];
+        m = max(m, max((u << 16) & 0x7FFFFFFFu, u & 0x7FFF0000u));
+    }
+    return m;
+}
+
+// n BF16 values at p (a multiple of 2) become FP16 values times 2^k, in place.
+__device__ __forceinline__ void bf16_to_f16_scaled(unsigned char* p, uint32_t n, int k, int tid, int nthr) {
+    uint32_t* q = reinterpret_cast<uint32_t*>(p);
+    const float sc = ldexpf(1.0f, k);
+    for (uint32_t i = tid; i < n / 2; i += nthr) {
+        const uint32_t u = q[i];
+        const __half2 h = __floats2half2_rn(__uint_as_float(u << 16) * sc, __uint_as_float(u & 0xFFFF0000u) * sc);
+        q[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
         tab_bar;
-    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t tmem_base, dmax_bits, xmax_bits;
     __shared__ int abort_flag, never;
     __shared__ int chunk_next[DSTAGE];  // next dynamically handed-out 256-entry block of the stage's chunk
     __shared__ double red[DSC_EPI_WARPS];
@@ -1128,8 +1232,37 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     float* wl = reinterpret_cast<float*>(Ss + DSTAGE * DS_BYTES);
     const uint32_t SBO_D = (uint32_t)(A.kp / 8) * 128u;
 
-    // D as the B operand: rows θ (N), K = atoms; bf16, zero-padded.
+    // D as the B operand: rows θ (N), K = atoms; BF16 (its stored precision),
+    // zero-padded, then FP16 times 2^kD in place.
+    if (tid == 0) dmax_bits = xmax_bits = 0u;
     stage_d<false>(A, Ds, SBO_D, tid, blockDim.x);
+    __syncthreads();
+    {
+        // max |D| (for kD) and max |x| over the weight gather's block maxima (for kS)
+        uint32_t dm = warp_max_u32(bf16_absmax_bits(Ds, (uint32_t)A.np * A.kp, tid, blockDim.x));
+        uint32_t xm = 0u;
+        for (int i = tid; i < A.n_xamax; i += blockDim.x) xm = max(xm, A.x_amax[i]);
+        xm = warp_max_u32(xm);
+        if (lane == 0) {
+            atomicMax(&dmax_bits, dm);
+            atomicMax(&xmax_bits, xm);
+        }
+    }
+    __syncthreads();
+    const int kD = f16_scale_exp(dmax_bits);
+    bf16_to_f16_scaled(Ds, (uint32_t)A.np * A.kp, kD, tid, blockDim.x);
+    // S = Σ_run val·x is stored as FP16 times 2^kS, with |S| <= run_vmax · max|x|
+    int kS = 0;
+    {
+        const float xmax = __uint_as_float(xmax_bits);
+        if (xmax_bits != 0u && xmax <= 3.0e38f && A.run_vmax > 0.0f) {
+            int ex = 0, er = 0;
+            (void)frexpf(xmax, &ex);
+            (void)frexpf(A.run_vmax, &er);
+            kS = max(-120, min(120, 15 - ex - er));
+        }
+    }
+    const float s_scale = ldexpf(1.0f, kS), y_unscale = ldexpf(1.0f, -kS - kD);
     if (tid == 0) {
         for (int s = 0; s < DSTAGE; ++s) {
             mbar_init(&full_bar[s], DSC_PROD_WARPS);
@@ -1232,7 +1365,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                         load_slot(A.soff, A, nbase, nxt);
                         pf = true;
                     }
-                    dsc_slot(A, cur, base, beg, end, wl, S, lane);
+                    dsc_slot(A, cur, base, beg, end, wl, S, lane, s_scale);
                     if (!more) break;
                     cur = nxt;
                     base = b2;
@@ -1309,8 +1442,10 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     const int64_t o = (int64_t)A.nt * v + j;
                     if (vec && j + cnt <= A.nt) {
                         for (int e = 0; e < cnt; e += 4) {
-                            float4 yv = make_float4(__uint_as_float(rr[e]), __uint_as_float(rr[e + 1]),
-                                                    __uint_as_float(rr[e + 2]), __uint_as_float(rr[e + 3]));
+                            float4 yv = make_float4(__uint_as_float(rr[e]) * y_unscale,
+                                                    __uint_as_float(rr[e + 1]) * y_unscale,
+                                                    __uint_as_float(rr[e + 2]) * y_unscale,
+                                                    __uint_as_float(rr[e + 3]) * y_unscale);
                             if (A.b) {
                                 const float4 bv = __ldg(reinterpret_cast<const float4*>(A.b + o + e));
                                 yv.x -= bv.x;
@@ -1325,7 +1460,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     } else {
                         for (int e = 0; e < cnt; ++e) {
                             if (j + e < A.nt) {
-                                float y = __uint_as_float(rr[e]);
+                                float y = __uint_as_float(rr[e]) * y_unscale;
                                 if (A.b) y -= A.b[o + e];
                                 if (wy) A.out[o + e] = y;
                                 sqf += y * y;
@@ -1352,8 +1487,8 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             if (lane == 0) red[q] = sq;
         }
     } else if (lane == 0) {
-        // ---------------- MMA issuer: Yᵀ[128 x np] = S[128 x kp] · Dᵀ
-        const uint32_t idesc = idesc_bf16_f32(128, (uint32_t)A.np);
+        // ---------------- MMA issuer: Yᵀ[128 x np] = S[128 x kp] · Dᵀ (FP16 operands)
+        const uint32_t idesc = idesc_f16_f32(128, (uint32_t)A.np);
         const uint32_t sS = smem_u32(Ss), sD = smem_u32(Ds);
         uint32_t cc = 0, tcount = 0;
         uint32_t zlast = 0;  // bit z: parity of the last zero-copy phase issued on stage z
@@ -1378,7 +1513,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     for (int kk = 0; kk < DKC / 16; ++kk) {
                         const uint64_t ad = smem_desc(sS + st * DS_BYTES + kk * 256u, 128u, DS_SBO);
                         const uint64_t bd = smem_desc(sD + (uint32_t)c * (DKC / 8) * 128u + kk * 256u, 128u, SBO_D);
-                        mma_bf16(d, ad, bd, idesc, (c | kk) != 0 ? 1u : 0u);
+                        mma_f16(d, ad, bd, idesc, (c | kk) != 0 ? 1u : 0u);
                     }
                     mma_commit(&empty_bar[st]);
                     // once these MMAs have read the stage, clear it for its next use
@@ -1445,8 +1580,9 @@ __host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, in
     return d + (uint32_t)rbufs * r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
-// FIXED: the table holds 32-bit integers in units of 1/sc (sc a power of two chosen
-// so that no partial sum can leave the int32 range); otherwise FP32.
+// FIXED: the table holds 32-bit integers in units of 1/sc' (sc' a power of two chosen
+// so that no partial sum can leave the int32 range); otherwise FP32.  sc carries
+// also the removal of the operand scales from Z: x = val·Z·sc is in table units.
 template <bool CHECK, bool FIXED>
 __device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Zw,
                                           float* gl, uint32_t gl_s, float sc) {
@@ -1457,8 +1593,8 @@ __device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg,
             if (idx < beg || idx >= end) continue;
         }
         const uint32_t k = u16_at(s.key, e);
-        const float x = bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)];
-        if (FIXED) atomicAdd(reinterpret_cast<int*>(gl) + u16_at(s.fl, e), __float2int_rn(x * sc));
+        const float x = bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)] * sc;
+        if (FIXED) atomicAdd(reinterpret_cast<int*>(gl) + u16_at(s.fl, e), __float2int_rn(x));
         else red_add_shared_f32(gl_s + 4u * u16_at(s.fl, e), x);
     }
 }
@@ -1537,7 +1673,7 @@ __global__ void __launch_bounds__(AMAX_THREADS) wc_amax_kernel(TcArgs A) {
 __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t r_full[2], r_empty[2], z_full[ZSLOTS], z_empty[ZSLOTS], fin_bar;
-    __shared__ uint32_t tmem_base, d1_bits;
+    __shared__ uint32_t tmem_base, d1_bits, dmax_bits;
     __shared__ int abort_flag, never;
     if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1567,6 +1703,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         abort_flag = 0;
         never = 0;
         d1_bits = 0u;
+        dmax_bits = 0u;
         fence_barrier_init();
     }
     if (warp == WC_MMA_WARP) {
@@ -1591,7 +1728,15 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             m = max(m, __float_as_uint(sum) & 0x7FFFFFFFu);
         }
         if (lane == 0 && m != 0u) atomicMax(&d1_bits, m);
+        const uint32_t dm = warp_max_u32(bf16_absmax_bits(Dw, (uint32_t)A.kp * A.np, tid, blockDim.x));
+        if (lane == 0) atomicMax(&dmax_bits, dm);
     }
+    __syncthreads();
+    // the MMA reads D as FP16 times 2^kD (the BF16 values, exactly); each tile's R
+    // as FP16 times 2^kR of its brick, so that Z in tensor memory is 2^(kR+kD) Z
+    const int kD = f16_scale_exp(dmax_bits);
+    bf16_to_f16_scaled(Dw, (uint32_t)A.kp * A.np, kD, tid, blockDim.x);
+    fence_proxy_async_smem();
     __syncthreads();
 
     if (warp < WC_SCAT_WARPS) {
@@ -1619,7 +1764,11 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             int bexp = 0;
             (void)frexpf(bnd, &bexp);
             const bool fixed = bnd <= 3.0e38f && bnd >= 1.0e-27f;
-            const float sc = fixed ? ldexpf(1.0f, 29 - bexp) : 0.0f, inv = fixed ? ldexpf(1.0f, bexp - 29) : 0.0f;
+            // Z in tensor memory carries the operand scales 2^(kR + kD); the table
+            // unit 2^(bexp - 29) is in true units (sc folds both in, exactly)
+            const int kZ = f16_scale_exp(am) + kD;
+            const float sc = fixed ? ldexpf(1.0f, 29 - bexp - kZ) : ldexpf(1.0f, -kZ),
+                        inv = fixed ? ldexpf(1.0f, bexp - 29) : 0.0f;
             // the table's global fascicle ids, read by the flush at the brick's end
             for (int i = 32 * tid; i < nfb; i += 32 * WC_SCAT_THREADS) prefetch_l2(A.brick_fasc + fb0 + i);
             if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
@@ -1721,7 +1870,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS, inv);
         }
     } else if (warp < WC_MMA_WARP) {
-        // ---------------- R tile loader: r[:, v] -> bf16 A operand (rows = voxels, K = θ)
+        // ---------------- R tile loader: r[:, v] -> FP16 A operand times 2^kR of the
+        // brick (rows = voxels, K = θ); kR from the brick's max |r|, as the scatter warps compute it
         const int lt = tid - WC_SCAT_THREADS;
         const int ngrp = A.np / 8;
         const bool vec = A.vec4 != 0 && (A.nt % 8) == 0;
@@ -1732,6 +1882,10 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             if (brick < 0) break;
             int r_next = r + 1;
             const int next_brick = live_brick(A, G, cta, r_next);
+            uint32_t am = 0u;
+            for (int i = 4 * A.brick_tile_ptr[brick] + lane; i < 4 * A.brick_tile_ptr[brick + 1]; i += 32)
+                am = max(am, A.tile_amax[i]);
+            const float rs = ldexpf(1.0f, f16_scale_exp(warp_max_u32(am)));
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
                 // R buffer rb, used for the k-th time (tiles go round the buffers)
                 const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
@@ -1772,10 +1926,10 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                         const int u = u0 + s * WC_LOAD_THREADS;
                         if (u >= total) continue;
                         const int row = u / ngrp, g8 = u % ngrp;
-                        __nv_bfloat162 p0 = __floats2bfloat162_rn(lo[s].x, lo[s].y);
-                        __nv_bfloat162 p1 = __floats2bfloat162_rn(lo[s].z, lo[s].w);
-                        __nv_bfloat162 p2 = __floats2bfloat162_rn(hi[s].x, hi[s].y);
-                        __nv_bfloat162 p3 = __floats2bfloat162_rn(hi[s].z, hi[s].w);
+                        __half2 p0 = __floats2half2_rn(lo[s].x * rs, lo[s].y * rs);
+                        __half2 p1 = __floats2half2_rn(lo[s].z * rs, lo[s].w * rs);
+                        __half2 p2 = __floats2half2_rn(hi[s].x * rs, hi[s].y * rs);
+                        __half2 p3 = __floats2half2_rn(hi[s].z * rs, hi[s].w * rs);
                         uint4 pk;
                         pk.x = *reinterpret_cast<uint32_t*>(&p0);
                         pk.y = *reinterpret_cast<uint32_t*>(&p1);
@@ -1812,8 +1966,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
         }
     } else if (lane == 0) {
         // ---------------- MMA issuer: Zᵀ[128 x kp] = R[128 x np] · Dᵀ, one 128-atom chunk
-        // (N = 128) at a time into the next slot of the tensor-memory ring
-        const uint32_t idesc = idesc_bf16_f32(128, 128u);
+        // (N = 128) at a time into the next slot of the tensor-memory ring (FP16 operands)
+        const uint32_t idesc = idesc_f16_f32(128, 128u);
         const uint32_t sR0 = smem_u32(Rs), sD = smem_u32(Dw);
         const int kc = A.kp / 128;
         uint32_t tcount = 0, kcount = 0;
@@ -1840,7 +1994,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                     for (int kk = 0; kk < A.np / 16; ++kk) {
                         const uint64_t ad = smem_desc(sR + kk * 256u, 128u, SBO_K);
                         const uint64_t bd = smem_desc(sD + (uint32_t)(16 * j) * SBO_K + kk * 256u, 128u, SBO_K);
-                        mma_bf16(tb + zs * 128u, ad, bd, idesc, kk != 0 ? 1u : 0u);
+                        mma_f16(tb + zs * 128u, ad, bd, idesc, kk != 0 ? 1u : 0u);
                     }
                     mma_commit(&z_full[zs]);
                 }
@@ -1903,6 +2057,7 @@ static TcArgs make_args(life_index_s* ix) {
     A.wb_ptr = L.wb_ptr.as<int32_t>();
     A.brick_cv = L.brick_cv.as<float>();
     A.tile_amax = L.tile_amax.as<uint32_t>();
+    A.run_vmax = L.run_vmax;
     A.nt = ix->nt;
     A.na = ix->na;
     A.np = L.np;
@@ -1942,10 +2097,13 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
             wb_gather_live_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(
                 L.wb_src.as<int32_t>(), L.wb_total, w, L.wb.as<float>(), L.wb_live.as<uint8_t>(),
                 L.sparse_ctl.as<SparseCtl>(), (unsigned long long)L.n_brick_slots,
-                !gate ? ALLOW_FREE : (gate_mode == GATE_ACTIVE ? ALLOW_NONE : ALLOW_BACKOFF), gate, gate_mode);
+                !gate ? ALLOW_FREE : (gate_mode == GATE_ACTIVE ? ALLOW_NONE : ALLOW_BACKOFF), gate, gate_mode,
+                L.x_amax.as<uint32_t>());
         else
             wb_gather_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(L.wb_src.as<int32_t>(), L.wb_total, w,
-                                                                      L.wb.as<float>());
+                                                                      L.wb.as<float>(), L.x_amax.as<uint32_t>());
+        A.x_amax = L.x_amax.as<uint32_t>();
+        A.n_xamax = ix->num_sms * 8;
         LIFE_CHECK_LAUNCH();
     }
     LIFE_CUDA_TRY(cudaFuncSetAttribute(dsc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -203,6 +203,20 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
            | ((M >> 4) << 24);  // M / 16
 }
 
+// Instruction descriptor, kind::f16: FP16 A and B (format 0), FP32 accumulator, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(uint32_t M, uint32_t N) {
+    return (1u << 4)            // D format: F32
+           | ((N >> 3) << 17)   // N / 8
+           | ((M >> 4) << 24);  // M / 16
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 with FP16 operands, one CTA (the
+// same instruction as mma_bf16; the operand type comes from the descriptor).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+}
+
 // Byte offset of element (row, k) in a K-major no-swizzle operand whose core
 // matrices along K are 128 bytes apart (lbo = 128) and whose 8-row groups are
 // `sbo` bytes apart; 2-byte elements.

@@ -13,12 +13,17 @@ sum's condition number).
 
 BF16 storage: the backward pass consumes the forward residual, so the forward
 rounding error reaches every gradient; the check is elementwise against bounds
-from the rounding model (u = 2^-8, each BF16 rounding a relative error <= u,
-FP32 accumulation negligible, a 1.25 safety factor):
-  forward   |δe[θ,v]| <= 1.25·3u·Σ|D[θ,a]·val·w[f]|          (val, S = Σ val·w, D rounded)
-  dL/dw     |δg[f]|   <= Σ val·|D|·(|δe| + 1.25·3u·|e|)       (r, D, val rounded in WC)
+from the rounding model (u = 2^-8 for each BF16 rounding of a stored value, u16 =
+2^-11 for the FP16 rounding of a tensor-core operand, FP32 accumulation
+negligible, a 1.25 safety factor):
+  forward   |δe[θ,v]| <= 1.25·(2u+u16)·Σ|D[θ,a]·val·w[f]|    (val and D stored, S = Σ val·w operand)
+  dL/dw     |δg[f]|   <= Σ val·|D|·(|δe| + 1.25·(2u+u16)·|e|)   (val and D stored, r operand in WC)
   dL/dD     |δG[θ,a]| <= Σ |val·w|·(|δe| + 1.25·2u·|e|)
   dL/dλ     |δ|       <= Σ |dD/dλ|·|δG|
+The relative L2 errors are reported against the 3e-3 gate of the reduced-precision
+forms: dL/dw is held to it; dL/dD (3.8e-3 measured) is the gradient of the
+BF16-stored model at its own residual, whose error relative to e = M w − r
+exceeds that of y, and is held to the elementwise bound above.
 """
 import numpy as np
 import pytest
@@ -91,14 +96,14 @@ def test_gradients_vs_oracle_bf16(life, case):
     L, gw, gD, glam = gpu_loss_and_grads(life, idx, p, w, r, p.lam)
     torch.cuda.synchronize()
     life.life_check_device_status()
-    u = 2.0 ** -8
+    u, u16 = 2.0 ** -8, 2.0 ** -11
     a = np.abs
     D64, _ = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)
     phi_abs = oracle.Phi(phi.atom, phi.voxel, phi.fasc, a(phi.val))
     nt, nv, nf, na = p.n_theta, p.n_voxels, p.n_fasc, p.n_atoms
     e_ref = oracle.dsc(phi, D64, w, nt, nv) - r
-    de = 1.25 * 3 * u * oracle.dsc(phi_abs, a(D64), a(w), nt, nv)
-    gw_bound = oracle.wc(phi_abs, a(D64), de + 1.25 * 3 * u * a(e_ref), nt, nf)
+    de = 1.25 * (2 * u + u16) * oracle.dsc(phi_abs, a(D64), a(w), nt, nv)
+    gw_bound = oracle.wc(phi_abs, a(D64), de + 1.25 * (2 * u + u16) * a(e_ref), nt, nf)
     gD_bound = oracle.grad_D(phi_abs, a(w), de + 1.25 * 2 * u * a(e_ref), nt, na)
     L_bound = float(a(e_ref) @ de + 0.5 * de @ de)
     assert abs(L - L_ref) <= L_bound, (L, L_ref, L_bound)
@@ -106,6 +111,7 @@ def test_gradients_vs_oracle_bf16(life, case):
     assert (a(gD - gD_ref) <= gD_bound).all(), float((a(gD - gD_ref) / gD_bound).max())
     assert abs(glam - glam_ref) <= float(a(dD64) @ gD_bound), (glam, glam_ref)
     print("bf16 rel L2: gw", rel(gw, gw_ref), "gD", rel(gD, gD_ref), "glam", abs(glam - glam_ref) / abs(glam_ref))
+    assert rel(gw, gw_ref) <= 3e-3, rel(gw, gw_ref)
     idx.close()
 
 

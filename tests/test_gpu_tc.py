@@ -1,7 +1,8 @@
 """GPU parity of the tensor-core (BF16-storage) path against the FP64 oracle.
 
-Tolerance: relative L2 error <= 3e-3 for the reduced-precision path (Φ values, D,
-and the on-chip S / r tiles are BF16; accumulation is FP32; reductions FP64).
+Tolerance: relative L2 error <= 3e-3 for the reduced-precision path (Φ values and D
+stored in BF16; the tensor-core operands S / r tiles and D in FP16 under exact
+power-of-two scales; accumulation FP32; reductions FP64).
 Every call is followed by a device-status check, so a bounded wait that gave up
 inside a kernel fails the test instead of passing silently.
 """
@@ -16,6 +17,8 @@ pytestmark = pytest.mark.gpu
 
 TOL_BF16 = 3e-3
 U_BF16 = 2.0 ** -8   # unit roundoff of BF16 (8 significand bits, round to nearest)
+U_F16 = 2.0 ** -11   # unit roundoff of FP16 (11 significand bits)
+U_TC = 2 * U_BF16 + U_F16   # per result: two BF16 roundings (Phi value, D) and one FP16 (S or r)
 
 
 def rel(a, b):
@@ -44,14 +47,16 @@ def tc_index(life, a, v, f, x, nt, na, nv, nf, ijk=None):
 
 
 def rounding_bounds(phi, D32, w, r, nt, nv, nf):
-    """First-order bounds on |GPU - exact| per output element.  DSC rounds three
-    quantities to BF16 (the Phi value, S = sum val*w, and D): |err| <= 3u sum|D||val w|.
-    WC rounds the value, D and r: |err| <= 3u sum_k |val| sum_t |D||r|.  FP32
-    accumulation adds far less and is covered by the factor 1.25."""
+    """First-order bounds on |GPU - exact| per output element.  DSC rounds the Phi
+    value and D to BF16 (stored precision) and S = sum val*w to FP16 (the MMA
+    operand): |err| <= (2u + u16) sum|D||val w|.  WC rounds the value and D to BF16
+    and r to FP16: |err| <= (2u + u16) sum_k |val| sum_t |D||r|.  The FP16 operand
+    scales are exact powers of two; FP32 accumulation adds far less and is covered
+    by the factor 1.25."""
     a = np.abs
     yb = oracle.dsc(oracle.Phi(phi.atom, phi.voxel, phi.fasc, a(phi.val)), a(D32), a(w), nt, nv)
     gb = oracle.wc(oracle.Phi(phi.atom, phi.voxel, phi.fasc, a(phi.val)), a(D32), a(r), nt, nf)
-    return 1.25 * 3 * U_BF16 * yb, 1.25 * 3 * U_BF16 * gb
+    return 1.25 * U_TC * yb, 1.25 * U_TC * gb
 
 
 def run_check(life, idx, phi, D32, nt, nv, nf, seed=0, tol=TOL_BF16, elementwise=False):
@@ -136,7 +141,7 @@ def test_tc_giant_voxel_and_empty(life):
 
 def test_tc_matches_simt_bf16_values(life):
     """Same BF16-rounded Φ values on both paths: the remaining difference is the
-    BF16 rounding of D and of the on-chip S / r tiles."""
+    BF16 rounding of D and the FP16 rounding of the on-chip S / r tiles."""
     p = synth.config_problem("tiny")
     D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
     i_tc = tc_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
