@@ -128,8 +128,9 @@ __device__ __forceinline__ void block_absmax_out(uint32_t m, uint32_t* out) {
 // this call's w, and per block the bits of max |w| over the gathered slots (the
 // scale of the DSC's FP16 S operand).  (n is a multiple of 4 and both arrays are
 // 16-byte aligned: each thread moves 4 slots per step with one 16-byte load of
-// indices, four independent gathers and one 16-byte store.)
-__global__ void wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
+// indices, four independent gathers and one 16-byte store.)  The launch (8 blocks
+// of 256 threads per SM) is one full wave only at <= 32 registers per thread.
+__global__ void __launch_bounds__(256, 8) wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
                                  float* __restrict__ wb, uint32_t* __restrict__ amax) {
     const int64_t n4 = n >> 2;
     uint32_t m = 0u;
@@ -234,7 +235,7 @@ __device__ void dsc_decide(SparseCtl* c, unsigned long long n_slots, int allow, 
 // L; the last block to finish takes the call's decision.
 constexpr int GATHER_THREADS = 256;
 
-__global__ void __launch_bounds__(GATHER_THREADS) wb_gather_live_kernel(const int32_t* __restrict__ wsrc, int64_t n,
+__global__ void __launch_bounds__(GATHER_THREADS, 8) wb_gather_live_kernel(const int32_t* __restrict__ wsrc, int64_t n,
                                                                         const float* __restrict__ w,
                                                                         float* __restrict__ wb,
                                                                         const uint8_t* __restrict__ live,
