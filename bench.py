@@ -40,10 +40,10 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "5aa5bffd72b8b43d57bd15e54f1ab2d9c8486f6ddc42ac15e4cfa346b34a47ae",
+    "sha256": "73b2dd1b6a4306f83f21a97f229b72e2abc6a2fead9865573b9126d62959f318",
     "nnz": 23816750,
-    "bytes": {"dsc": (11036416 + 0) + (193704448 + 16558080),
-              "wc": (39992576 + 0) + (202005504 + 70656)},
+    "bytes": {"dsc": (11041792 + 0) + (193712640 + 16351232),
+              "wc": (39992832 + 0) + (202023936 + 66816)},
 }
 
 
