@@ -369,11 +369,11 @@ def sparse_dsc_sweep(life, live, full, fracs=(0.0, 0.5, 0.9, 0.97), reps=10):
     return out
 
 
-def time_to_tolerance(life, lo, hi, tol, tol_lo=1e-3, max_iter=500):
+def time_to_tolerance(life, lo, hi, tol, switches=(1e-3, 3e-4, 1e-4), max_iter=500):
     """Time to ‖g~‖ <= tol·‖g~_0‖ from w = 1: the plain path `hi` alone, the fast
-    path `lo` alone, and `lo` until tol_lo followed by `hi` to tol from the same w
-    and state (the state keeps ‖g~_0‖, so both phases test against the same
-    reference).  Graphs are built by untimed calls first."""
+    path `lo` alone, and `lo` until each switch tolerance followed by `hi` to tol
+    from the same w and state (the state keeps ‖g~_0‖, so both phases test against
+    the same reference).  Graphs are built by untimed calls first."""
     import torch
     s = torch.cuda.current_stream()
 
@@ -390,7 +390,7 @@ def time_to_tolerance(life, lo, hi, tol, tol_lo=1e-3, max_iter=500):
         return {"iters": int(x["it"]), "converged": int(x["converged"]), "obj": x["obj"],
                 "rel_pg": (x["gg"] / x["gg0"]) ** 0.5 if x["gg0"] > 0 else None}
 
-    out = {"tol": tol, "tol_switch": tol_lo, "max_iter": max_iter}
+    out = {"tol": tol, "max_iter": max_iter}
     for name, path in (("plain", hi), ("fast", lo)):
         path.reset()
         life.life_sbbnnls_solve(path.idx, path.D, path.b, path.w, 1, path.st, path.ws, tol=tol)
@@ -400,19 +400,29 @@ def time_to_tolerance(life, lo, hi, tol, tol_lo=1e-3, max_iter=500):
                                                   tol=tol))
         out[name] = dict(state(path.st), s=t)
 
-    def mixed():
-        life.life_sbbnnls_solve(lo.idx, lo.D, lo.b, lo.w, max_iter, lo.st, lo.ws, tol=tol_lo)
-        life.life_sbb_state_resume(lo.st)
-        life.life_sbbnnls_solve(hi.idx, hi.D, hi.b, lo.w, max_iter, lo.st, hi.ws, tol=tol)
+    out["fast_then_plain"] = {}
+    for tol_lo in switches:
+        def mixed():
+            life.life_sbbnnls_solve(lo.idx, lo.D, lo.b, lo.w, max_iter, lo.st, lo.ws, tol=tol_lo)
+            ph1 = life.read_sbb_state(lo.st)["it"] if timing_phase1 else None
+            life.life_sbb_state_resume(lo.st)
+            life.life_sbbnnls_solve(hi.idx, hi.D, hi.b, lo.w, max_iter, lo.st, hi.ws, tol=tol)
+            return ph1
 
-    lo.reset()
-    mixed()
-    torch.cuda.synchronize()
-    lo.reset()
-    t = timed(mixed)
-    out["fast_then_plain"] = dict(state(lo.st), s=t)
-    if out["plain"]["converged"] and out["fast_then_plain"]["converged"]:
-        out["speedup_at_tol"] = out["plain"]["s"] / t
+        timing_phase1 = True
+        lo.reset()
+        it_fast = mixed()
+        torch.cuda.synchronize()
+        timing_phase1 = False
+        lo.reset()
+        t = timed(mixed)
+        row = dict(state(lo.st), s=t, iters_fast=int(it_fast))
+        out["fast_then_plain"][f"{tol_lo:g}"] = row
+    done = {k: v for k, v in out["fast_then_plain"].items() if v["converged"]}
+    if out["plain"]["converged"] and done:
+        best = min(done, key=lambda k: done[k]["s"])
+        out["best_switch"] = best
+        out["speedup_at_tol"] = out["plain"]["s"] / done[best]["s"]
     return out
 
 

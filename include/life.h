@@ -172,6 +172,11 @@ LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, 
  * table slots non-zero) it streams only the live entries, rebuilding that stream
  * for w's support when it is stale or much larger than needed.  The result is
  * that of the full stream up to the association of FP32 run sums.
+ * Precision on a TC index: Phi values and D are stored in BF16; the tensor cores
+ * read D and S = Σ val·w as FP16 under exact power-of-two scales (D's from its
+ * largest value, S's from max |w| and the largest run of Phi values), FP32
+ * accumulation.  A run sum more than ~2^40 below the largest possible one in the
+ * call underflows FP16 and contributes zero.
  * Errors: LIFE_EINVAL when D, w or both y and sumsq are NULL.
  */
 LIFE_API life_status life_dsc(life_index idx, const float* D, const float* w, const float* b, float* y,
@@ -196,6 +201,12 @@ LIFE_API life_status life_index_sparse_stats(life_index idx, int64_t* out, void*
  *  r      float32 [Nθ·Nv]
  *  g      float32 [Nf] output (fully overwritten)
  *  sumsq  double [1] output or NULL: Σ_f g[f]^2 in FP64
+ * Precision on a TC index: Phi values and D stored in BF16; each 128-voxel tile
+ * of r is read by the tensor cores as FP16 under a power-of-two scale taken from
+ * the max |r| of its brick (values more than ~2^40 below it underflow; a brick
+ * holding a NaN or inf of r is read unscaled, so there |r| > 65504 becomes inf);
+ * the per-brick partial sums are 32-bit fixed point in a unit relative to the
+ * brick's largest possible sum, FP32 where that bound is not a normal float.
  */
 LIFE_API life_status life_wc(life_index idx, const float* D, const float* r, float* g, double* sumsq,
                     void* stream);

@@ -341,3 +341,34 @@ def test_wc_non_finite_residual(life):
     r0 = np.where(np.isfinite(r), r, 0.0).astype(np.float32)
     _, gb = rounding_bounds(phi, D32, np.zeros(nf, np.float32), r0, nt, nv, nf)
     assert (np.abs(g[ok] - g_ref[ok]) <= gb[ok] + 1e-30).all()
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e12, 1e30])
+def test_tc_operand_scales(life, scale):
+    """The FP16 tensor-core operands carry exact power-of-two scales chosen per call
+    (S, from max |w|) and per brick (the r tile, from its max |r|): weights and
+    residuals far outside FP16's range give the same relative accuracy as at unit
+    scale, and the results scale exactly with the inputs up to rounding."""
+    p, D32, phi, idx = tiny_case(life)
+    nt, nv, nf = p.n_theta, p.n_voxels, p.n_fasc
+    rng = np.random.default_rng(31)
+    w = (rng.random(nf) * scale).astype(np.float32)
+    w[rng.random(nf) < 0.3] = 0.0
+    r = (rng.standard_normal(nt * nv) * scale).astype(np.float32)
+    D = dev(D32)
+    y, _ = life.life_dsc(idx, D, dev(w))
+    g, _ = life.life_wc(idx, D, dev(r))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    y, g = y.cpu().numpy(), g.cpu().numpy()
+    y_ref = oracle.dsc(phi, D32, w, nt, nv)
+    g_ref = oracle.wc(phi, D32, r, nt, nf)
+    yb, gb = rounding_bounds(phi, D32, w, r, nt, nv, nf)
+    assert np.isfinite(y).all() and np.isfinite(g).all()
+    assert (np.abs(y - y_ref) <= yb + 1e-38).all(), float((np.abs(y - y_ref) / (yb + 1e-38)).max())
+    # WC's fixed-point tables round each entry to a unit relative to its brick's bound
+    tiles = {k: v.cpu().numpy() for k, v in life.life_index_export_tiles(idx).items()}
+    fxb = fixed_point_bound(phi, D32, r, tiles["tile_vox"][:128 * idx.info()["n_tiles"]], tiles["brick_tile_ptr"],
+                            nt, nv, nf)
+    assert (np.abs(g - g_ref) <= gb + fxb + 1e-38).all()
+    assert rel(y, y_ref) <= TOL_BF16 and rel(g, g_ref) <= TOL_BF16
