@@ -303,6 +303,21 @@ def job_throughput(steps, world, dt_max):
     return world * steps / dt_max
 
 
+def host_cpu():
+    """The host CPU as lscpu names it (architecture, model, CPUs)."""
+    import platform
+    desc = {"arch": platform.machine(), "cpus": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Vendor ID", "Core(s) per socket", "Core(s) per cluster", "Socket(s)"):
+                desc[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return desc
+
+
 def cpu_allcores_baseline(p, D32, b, reps=2):
     """The FP64 baseline as it stands on all host cores (the oracle's arithmetic
     with Phi grouped by voxel for DSC and by fascicle for WC, OpenMP), on the whole
@@ -665,6 +680,7 @@ def run_ours(args):
                       "index_build_s": v["path"].build_s} for k, v in results.items()},
         "vs_plain_fp32": (args.steps / best["dt"]) / (args.steps / results["fp32-simt"]["dt"]),
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                         "host": host_cpu(),
                          "sample": "%d FP64 SBB iterations of the whole workload (all %d raw entries) after one "
                                    "untimed, on %d host threads (OpenMP: voxel-grouped DSC, fascicle-grouped WC); "
                                    "grouping the entries took %.1f s" % (cpu["reps"], p.n_raw, cpu["cores"],
@@ -719,7 +735,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_desc(p), "path": "oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "final_state": {"it": st.it, "obj": st.obj}}
     print(json.dumps(line))

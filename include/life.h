@@ -337,8 +337,9 @@ LIFE_API life_status life_sbbnnls_solve(life_index idx, const float* D, const fl
  *  voxel_ijk                optional device int32 [n_voxels·3] of the whole problem
  *  opts, stream, out        as for life_build_index
  * Synchronizes `stream`; allocates temporary device memory.
- * Errors: LIFE_EINVAL for a range outside [0, n_voxels) or an empty range, and
- * the errors of life_build_index for the shard's entries.
+ * Errors: LIFE_EINVAL for a range outside [0, n_voxels) or an empty range;
+ * LIFE_ERANGE when any entry's voxel lies outside [0, n_voxels) (it would belong
+ * to no shard); the errors of life_build_index for the shard's entries.
  */
 LIFE_API life_status life_build_index_shard(const int32_t* atom, const int32_t* voxel, const int32_t* fasc,
                                             const float* val, int64_t nnz, int32_t n_theta, int32_t n_atoms,

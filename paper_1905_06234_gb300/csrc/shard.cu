@@ -12,12 +12,17 @@ life_status sbb_enqueue_shard_phase(life_index_s* ix, const float* D, const floa
                                     double* scal, life_sbb_state* st, void* workspace, double tol, int eq7_on_even,
                                     int phase, cudaStream_t s);
 
-__global__ void shard_flag_kernel(const int32_t* __restrict__ voxel, int64_t n, int32_t v0, int32_t v1,
-                                  int32_t* __restrict__ flag) {
+// flag[i] = entry i lies in the voxel range; *bad = 1 if any voxel id lies outside
+// [0, nv) (such an entry belongs to no shard, so the caller gets an error).
+__global__ void shard_flag_kernel(const int32_t* __restrict__ voxel, int64_t n, int32_t v0, int32_t v1, int32_t nv,
+                                  int32_t* __restrict__ flag, int32_t* __restrict__ bad) {
+    bool oor = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = voxel[i];
         flag[i] = (v >= v0 && v < v1) ? 1 : 0;
+        oor |= v < 0 || v >= nv;
     }
+    if (__any_sync(0xffffffffu, oor) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
 // Entries of the range, in input order, with voxel ids relative to v0.
@@ -64,18 +69,26 @@ extern "C" life_status life_build_index_shard(const int32_t* atom, const int32_t
     const int32_t* ijk = voxel_ijk ? voxel_ijk + 3 * (int64_t)v_begin : nullptr;
     if (nnz == 0)
         return life_build_index(atom, voxel, fasc, val, 0, n_theta, n_atoms, nv, n_fasc, ijk, opts, stream, out);
-    TmpBuf flag, pos;
+    TmpBuf flag, pos, bad;
     LIFE_TRY(flag.alloc(sizeof(int32_t) * (size_t)nnz, s));
     LIFE_TRY(pos.alloc(sizeof(int32_t) * (size_t)nnz, s));
+    LIFE_TRY(bad.alloc(sizeof(int32_t), s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), s));
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((nnz + 255) / 256, (int64_t)device_sm_count() * 16));
-    shard_flag_kernel<<<grid, 256, 0, s>>>(voxel, nnz, v_begin, v_end, flag.as<int32_t>());
+    shard_flag_kernel<<<grid, 256, 0, s>>>(voxel, nnz, v_begin, v_end, n_voxels, flag.as<int32_t>(),
+                                           bad.as<int32_t>());
     LIFE_CHECK_LAUNCH();
     LIFE_TRY(exclusive_scan_i32(flag.as<int32_t>(), pos.as<int32_t>(), nnz, s));
-    int32_t last[2];
+    int32_t last[3];
     LIFE_CUDA_TRY(cudaMemcpyAsync(&last[0], pos.as<int32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
     LIFE_CUDA_TRY(cudaMemcpyAsync(&last[1], flag.as<int32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+    LIFE_CUDA_TRY(cudaMemcpyAsync(&last[2], bad.p, 4, cudaMemcpyDeviceToHost, s));
     LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (last[2]) {
+        set_error("life_build_index_shard: a voxel index lies outside [0, %d)", n_voxels);
+        return LIFE_ERANGE;
+    }
     const int64_t m = (int64_t)last[0] + last[1];
     TmpBuf a, v, f, x;
     LIFE_TRY(a.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));

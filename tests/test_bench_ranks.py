@@ -52,3 +52,23 @@ def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(2.5, None, None) == 2.5
     assert bench.job_throughput(10, 1, 2.0) == 5.0
+
+
+def test_reference_arm_contract():
+    """bench.py --impl reference on the small workload: one JSON line whose steps
+    were all timed (ms_per_step x steps is the time that ran), on the host cores
+    it reports, with the reference-arm keys the contract asks for."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "tiny",
+                        "--steps", "3", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 3
+    assert line["unit"] == "iter/s" and line["higher_is_better"] is True
+    assert line["value"] == pytest.approx(1e3 / line["ms_per_step"], rel=1e-9)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["final_state"]["it"] == 6   # warm-up and timed steps, every one a full iteration

@@ -133,3 +133,25 @@ def test_sharded_solve_tracks_unsharded(life, case):
     # the same arithmetic up to the summation order of the exchanged sums
     assert rel(shards[0].w.cpu().numpy(), w1.cpu().numpy()) <= 1e-4
     assert abs(s2["obj"] - s1["obj"]) <= 1e-4 * s1["obj"]
+
+
+def test_shard_index_errors(life, case):
+    p, D32, phi, b = case
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).cuda().to(dt)
+    a, f = dev(p.coo_atom, torch.int32), dev(p.coo_fasc, torch.int32)
+    v = dev(p.coo_voxel, torch.int32)
+    x = dev(p.coo_val, torch.float32)
+    args = (p.n_theta, p.n_atoms, p.n_voxels, p.n_fasc)
+    for v0, v1 in ((5, 5), (-1, 10), (0, p.n_voxels + 1), (20, 10)):
+        with pytest.raises(life.LifeError) as e:
+            life.life_build_index_shard(a, v, f, x, *args, v0, v1)
+        assert e.value.status == 1   # LIFE_EINVAL
+    bad = v.clone()
+    bad[len(bad) // 2] = p.n_voxels   # belongs to no shard
+    with pytest.raises(life.LifeError) as e:
+        life.life_build_index_shard(a, bad, f, x, *args, 0, p.n_voxels // 2)
+    assert e.value.status == 2   # LIFE_ERANGE
+    # a range holding no entries at all is a valid, empty shard
+    empty = torch.zeros_like(v)   # every entry in voxel 0
+    ix = life.life_build_index_shard(a, empty, f, x, *args, 1, p.n_voxels)
+    assert ix.nnz == 0
