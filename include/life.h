@@ -149,7 +149,7 @@ LIFE_API life_status life_index_export_voxel_streams(life_index idx, int32_t* vo
  *  brick_fasc_ptr [n_bricks+1], brick_fasc [n_brick_fasc]  brick-local fascicle tables
  *  brick_order [n_bricks]        processing order
  *  va, fl [nnz] (uint16)         row | atom << 7;  brick-local fascicle | 0x8000 on run continuation
- *  val [nnz]                     BF16 values widened to float32
+ *  val [nnz]                     stored values as float32 (BF16 storage: widened; FP32: as stored)
  * Device outputs; any may be NULL.  Synchronizes `stream`.
  */
 LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* sub_ptr,

@@ -229,7 +229,9 @@ life_status autotune_tc(life_index_s* ix, cudaStream_t s) {
             LIFE_TRY(time_ms(s, 3, &t_dsc, tune_dsc, &c));
             for (int wg : {4, 2, 1}) {
                 ix->wc_groups = wg;
-                if (wc_effective_groups(ix) != wg) continue;
+                // the WC of an FP32-storage index runs on the CUDA cores: one timing
+                if (!ix->tile.wc_stream && wg != 4) continue;
+                if (ix->tile.wc_stream && wc_effective_groups(ix) != wg) continue;
                 float t_wc = 0.0f;
                 LIFE_TRY(time_ms(s, 3, &t_wc, tune_wc, &c));
                 const double cost = 2.0 * t_dsc + 1.5 * t_wc;
@@ -420,7 +422,7 @@ extern "C" life_status life_batch_get_info(life_batch batch, life_batch_info* ou
     I.n_fasc = ix->nf;
     const bool tc = ix->algo == LIFE_ALGO_TC && ix->tile.built;
     I.brick_edge = tc ? ix->tile.brick_edge : 0;
-    I.wc_groups = tc ? wc_effective_groups(ix) : 0;
+    I.wc_groups = tc && ix->tile.wc_stream ? wc_effective_groups(ix) : 0;
     I.tc_grid = tc ? bi.tc_grid : 0;
     I.simt_grid = tc ? 0 : bi.simt_grid;
     I.tuned = ix->tuned;

@@ -66,7 +66,8 @@ life_status spmv_wc(life_index_s* ix, const float* D, const float* r, float* g, 
     } else {
         LIFE_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * (size_t)ix->nf, s));
     }
-    if (use_tc(ix)) return wc_tc(ix, D, r, g, gate, gate_mode, s, bg, r_is_dsc_out);
+    // an FP32-storage TC index runs its DSC on the tensor cores and its WC on the CUDA cores
+    if (use_tc(ix) && ix->tile.wc_stream) return wc_tc(ix, D, r, g, gate, gate_mode, s, bg, r_is_dsc_out);
     return wc_simt(ix, D, r, g, gate, gate_mode, s, bg);
 }
 
@@ -83,13 +84,10 @@ life_status build_index_layouts(life_index_s* ix, const int32_t* atom, const int
         set_error("life_build_index: cannot allocate the device status word");
         return LIFE_ENOMEM;
     }
-    // The tensor-core path stores BF16; FP32 storage runs on CUDA cores.
+    // AUTO: the tensor-core kernels for BF16 storage, the CUDA-core kernels for FP32
+    // storage (whose TC form, split FP16 operands, is asked for explicitly).
     int algo = algo_req;
     if (algo == LIFE_ALGO_AUTO) algo = ix->precision == LIFE_BF16 ? LIFE_ALGO_TC : LIFE_ALGO_SIMT;
-    if (algo == LIFE_ALGO_TC && ix->precision != LIFE_BF16) {
-        set_error("life_build_index: the tensor-core path stores Phi and D in BF16 (precision = LIFE_BF16)");
-        return LIFE_ENOTSUP;
-    }
     ix->algo = algo;
     LIFE_TRY(build_voxel_layout(ix, atom, voxel, fasc, val, s));
     if (voxel_ijk) {
@@ -244,14 +242,15 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
     for (auto* b : bufs) tot += (int64_t)b->bytes;
     I.device_bytes = tot;
     if (idx->algo == LIFE_ALGO_TC && idx->tile.built)
-        I.stream_bytes = idx->tile.n_nnz * 6 + (int64_t)idx->tile.n_tiles * (TILE_V + idx->tile.n_sub) * 4;
+        I.stream_bytes = idx->tile.n_nnz * (4 + idx->tile.vbytes) +
+                         (int64_t)idx->tile.n_tiles * (TILE_V + idx->tile.n_sub) * 4;
     else
         I.stream_bytes = idx->nnz * (2 + 4 + (idx->precision == LIFE_BF16 ? 2 : 4)) + 4 * ((int64_t)idx->nv + 1);
     if (idx->tile.built) {
         I.n_brick_fasc = (int64_t)(idx->tile.brick_fasc.bytes / sizeof(int32_t));
         I.n_sub = idx->tile.n_sub;
         I.brick_edge = idx->tile.brick_edge;
-        I.wc_groups = wc_effective_groups(idx);
+        I.wc_groups = idx->tile.wc_stream ? wc_effective_groups(idx) : 0;
     }
     *out = I;
     return LIFE_OK;

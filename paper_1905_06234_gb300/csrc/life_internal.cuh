@@ -149,7 +149,10 @@ struct TileLayout {
     DevBuf wval;             // bf16 [n_nnz]
     DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom sub)
     DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
-    DevBuf val;              // bf16 [n_nnz]
+    DevBuf val;              // [n_nnz] stored values: bf16 (vbytes 2) or float (vbytes 4)
+    int vbytes = 2;          // bytes per stored value: 2 for BF16 storage, 4 for FP32 storage
+    bool wc_stream = true;   // the WC streams and their per-brick bounds exist (BF16 storage: the
+                             // FP32-storage index runs WC on the CUDA cores)
     // DSC brick weight tables: brick b's weights w[brick_fasc[...]] are gathered,
     // before each DSC launch, into wb[wb_ptr[b] ..) (16-byte aligned, padded to a
     // multiple of 4 floats) so a CTA loads a brick's table with one bulk copy

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "life_internal.cuh"
@@ -429,11 +430,18 @@ __global__ void local_fasc_kernel(const uint64_t* __restrict__ key2, const uint3
     }
 }
 
+// Stored values: BF16 (rounded once from the merged FP32 value) or FP32 (as merged).
+__device__ __forceinline__ void store_val(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+__device__ __forceinline__ void store_val(float* p, float x) { *p = x; }
+__device__ __forceinline__ float load_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float load_val(const float* p) { return *p; }
+
 // Entry streams in tile order, the continuation flag, and the sub-chunk offsets.
+template <class VT>
 __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ spay, int64_t m,
                                    int bf, const float* __restrict__ uval, int32_t n_sub, int64_t n_segs,
                                    uint16_t* __restrict__ va, uint16_t* __restrict__ soff,
-                                   uint16_t* __restrict__ fl, __nv_bfloat16* __restrict__ val,
+                                   uint16_t* __restrict__ fl, VT* __restrict__ val,
                                    int32_t* __restrict__ sub_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = skey[j];
@@ -441,7 +449,7 @@ __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint
         const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
         va[j] = (uint16_t)(row | (a << 7));
         soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) >> 1);
-        val[j] = __float2bfloat16_rn(uval[spay[j]]);
+        store_val(val + j, uval[spay[j]]);
         if (j > 0 && (skey[j - 1] >> bf) == (k >> bf)) fl[j] = (uint16_t)(fl[j] | CONT);
         const int64_t seg = (int64_t)t * n_sub + (a >> 5);
         int64_t segp = -1;
@@ -500,13 +508,14 @@ __global__ void fill_kernel(int32_t* p, int64_t n, int32_t v) {
 // Bits of the largest Σ|val| over the entries of one (atom, voxel) run of the DSC
 // stream (a run starts at an entry without the continuation flag): with max |x|
 // it bounds every S value of a DSC.
-__global__ void run_vmax_kernel(const uint16_t* __restrict__ fl, const __nv_bfloat16* __restrict__ val, int64_t m,
+template <class VT>
+__global__ void run_vmax_kernel(const uint16_t* __restrict__ fl, const VT* __restrict__ val, int64_t m,
                                 uint32_t* __restrict__ out) {
     uint32_t best = 0u;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         if (fl[j] & CONT) continue;
-        float sum = fabsf(__bfloat162float(val[j]));
-        for (int64_t k = j + 1; k < m && (fl[k] & CONT); ++k) sum += fabsf(__bfloat162float(val[k]));
+        float sum = fabsf(load_val(val + j));
+        for (int64_t k = j + 1; k < m && (fl[k] & CONT); ++k) sum += fabsf(load_val(val + k));
         best = max(best, __float_as_uint(sum));
     }
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -602,7 +611,19 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         set_error("tensor-core path: too many fascicles");
         return LIFE_ENOTSUP;
     }
+    if (ix->precision == LIFE_FP32 && ix->na > 384) {
+        // D's two FP16 parts (Na/2 columns each) and the 128-column accumulator share
+        // the 512 tensor-memory columns of an SM
+        set_error("FP32 tensor-core DSC supports Na <= 384 (got %d)", ix->na);
+        return LIFE_ENOTSUP;
+    }
+    if (ix->precision == LIFE_FP32 && ix->sparse_dsc) {
+        set_error("the live-entry DSC stream is built for BF16 storage only");
+        return LIFE_ENOTSUP;
+    }
     const int64_t m = ix->nnz;
+    L.vbytes = ix->precision == LIFE_FP32 ? 4 : 2;
+    L.wc_stream = L.vbytes == 2;
     L.np = (ix->nt + 15) / 16 * 16;
     L.kp = (ix->na + 127) / 128 * 128;   // whole 128-atom DSC chunks
     L.n_sub = L.kp / SUB;
@@ -746,22 +767,27 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     LIFE_TRY(L.va.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.soff.alloc(sizeof(uint16_t) * m_pad));
     LIFE_TRY(L.fl.alloc(sizeof(uint16_t) * m_pad));
-    LIFE_TRY(L.val.alloc(sizeof(__nv_bfloat16) * m_pad));
+    LIFE_TRY(L.val.alloc((size_t)L.vbytes * m_pad));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.va.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.soff.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.fl.p, 0, sizeof(uint16_t) * m_pad, s));
-    LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+    LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, (size_t)L.vbytes * m_pad, s));
     LIFE_TRY(L.sub_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
     if (m > 0) {
         local_fasc_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
                                                     head.as<int32_t>(), uidx.as<int32_t>(), L.brick_fasc_ptr.as<int32_t>(),
                                                     L.fl.as<uint16_t>());
         LIFE_CHECK_LAUNCH();
-        tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
-                                                     ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
-                                                     L.soff.as<uint16_t>(),
-                                                     L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(),
-                                                     L.sub_ptr.as<int32_t>());
+        if (L.vbytes == 4)
+            tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
+                                                         ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                         L.soff.as<uint16_t>(), L.fl.as<uint16_t>(), L.val.as<float>(),
+                                                         L.sub_ptr.as<int32_t>());
+        else
+            tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
+                                                         ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                         L.soff.as<uint16_t>(), L.fl.as<uint16_t>(),
+                                                         L.val.as<__nv_bfloat16>(), L.sub_ptr.as<int32_t>());
         LIFE_CHECK_LAUNCH();
     } else {
         fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.sub_ptr.as<int32_t>(), n_segs + 1, 0);
@@ -772,7 +798,11 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         TmpBuf rv;
         LIFE_TRY(rv.alloc(sizeof(uint32_t), s));
         LIFE_CUDA_TRY(cudaMemsetAsync(rv.p, 0, sizeof(uint32_t), s));
-        run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), m, rv.as<uint32_t>());
+        if (L.vbytes == 4)
+            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<float>(), m, rv.as<uint32_t>());
+        else
+            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), m,
+                                                      rv.as<uint32_t>());
         LIFE_CHECK_LAUNCH();
         uint32_t bits = 0u;
         LIFE_CUDA_TRY(cudaMemcpyAsync(&bits, rv.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -783,25 +813,32 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     LIFE_CUDA_TRY(cudaMemsetAsync(L.x_amax.p, 0, sizeof(uint32_t) * (size_t)std::max(ix->num_sms, 1) * 8, s));
     // WC streams (row quarter major inside each tile)
     const int64_t n_wsegs = H.n_tiles * 4 * L.n_sub;
-    LIFE_TRY(L.wkey.alloc(sizeof(uint16_t) * m_pad));
-    LIFE_TRY(L.wfl.alloc(sizeof(uint16_t) * m_pad));
-    LIFE_TRY(L.wval.alloc(sizeof(__nv_bfloat16) * m_pad));
-    LIFE_TRY(L.wseg_ptr.alloc(sizeof(int32_t) * (n_wsegs + 1)));
-    LIFE_CUDA_TRY(cudaMemsetAsync(L.wkey.p, 0, sizeof(uint16_t) * m_pad, s));
-    LIFE_CUDA_TRY(cudaMemsetAsync(L.wfl.p, 0, sizeof(uint16_t) * m_pad, s));
-    LIFE_CUDA_TRY(cudaMemsetAsync(L.wval.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
-    if (m > 0) {
-        wc_key_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), m, bf, key2.as<uint64_t>(), pay2.as<uint32_t>());
-        LIFE_CHECK_LAUNCH();
-        LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, nbits64(H.n_tiles) + 16 + bf, s));
-        wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
-                                                   L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub, n_wsegs,
-                                                   L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
-                                                   L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
-        LIFE_CHECK_LAUNCH();
+    if (L.wc_stream) {
+        LIFE_TRY(L.wkey.alloc(sizeof(uint16_t) * m_pad));
+        LIFE_TRY(L.wfl.alloc(sizeof(uint16_t) * m_pad));
+        LIFE_TRY(L.wval.alloc(sizeof(__nv_bfloat16) * m_pad));
+        LIFE_TRY(L.wseg_ptr.alloc(sizeof(int32_t) * (n_wsegs + 1)));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.wkey.p, 0, sizeof(uint16_t) * m_pad, s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.wfl.p, 0, sizeof(uint16_t) * m_pad, s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.wval.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+        if (m > 0) {
+            wc_key_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), m, bf, key2.as<uint64_t>(), pay2.as<uint32_t>());
+            LIFE_CHECK_LAUNCH();
+            LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, nbits64(H.n_tiles) + 16 + bf, s));
+            wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
+                                                       L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub, n_wsegs,
+                                                       L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
+                                                       L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
+            LIFE_CHECK_LAUNCH();
+        } else {
+            fill_kernel<<<grid1d(n_wsegs + 1), 256, 0, s>>>(L.wseg_ptr.as<int32_t>(), n_wsegs + 1, 0);
+            LIFE_CHECK_LAUNCH();
+        }
     } else {
-        fill_kernel<<<grid1d(n_wsegs + 1), 256, 0, s>>>(L.wseg_ptr.as<int32_t>(), n_wsegs + 1, 0);
-        LIFE_CHECK_LAUNCH();
+        L.wkey.release();
+        L.wfl.release();
+        L.wval.release();
+        L.wseg_ptr.release();
     }
     LIFE_TRY(upload(L.tile_vox, H.tile_vox, s));
     LIFE_TRY(upload(L.brick_tile_ptr, H.brick_tile_ptr, s));
@@ -833,7 +870,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     }
     LIFE_TRY(L.brick_cv.alloc(sizeof(float) * std::max<int64_t>(H.n_bricks, 1)));
     LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * 4 * std::max<int64_t>(H.n_tiles, 1)));
-    if (H.n_bricks > 0) {
+    if (H.n_bricks > 0 && L.wc_stream) {
         const int cv_smem = (int)sizeof(int32_t) * std::max(L.max_fb, 1);
         LIFE_CUDA_TRY(cudaFuncSetAttribute(brick_cv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cv_smem));
         brick_cv_kernel<<<(unsigned)std::min<int64_t>(H.n_bricks, 65535), 256, cv_smem, s>>>(
@@ -884,8 +921,12 @@ life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, 
     LIFE_TRY(cp(va, L.va, sizeof(uint16_t) * L.n_nnz));
     LIFE_TRY(cp(fl, L.fl, sizeof(uint16_t) * L.n_nnz));
     if (val && L.n_nnz > 0) {
-        widen_bf16_kernel<<<grid1d(L.n_nnz), 256, 0, s>>>(L.val.as<__nv_bfloat16>(), L.n_nnz, val);
-        LIFE_CHECK_LAUNCH();
+        if (L.vbytes == 4) {
+            LIFE_TRY(cp(val, L.val, sizeof(float) * L.n_nnz));
+        } else {
+            widen_bf16_kernel<<<grid1d(L.n_nnz), 256, 0, s>>>(L.val.as<__nv_bfloat16>(), L.n_nnz, val);
+            LIFE_CHECK_LAUNCH();
+        }
     }
     LIFE_CUDA_TRY(cudaStreamSynchronize(s));
     return LIFE_OK;
@@ -913,6 +954,7 @@ struct TcArgs {
     const float* b;      // DSC residual or NULL
     float* out;          // DSC: y (or NULL);   WC: g (zeroed by the caller)
     double* partial;     // DSC: per-CTA FP64 Σ out²
+    const float* val32;  // DSC on an FP32-storage index: the stream's values (val is then unused)
     const float* wb;     // DSC: gathered brick weight tables
     const int32_t* wb_ptr;
     const float* brick_cv;    // WC: per-brick bound on Σ|val| of one fascicle
@@ -990,6 +1032,34 @@ __device__ __forceinline__ uint32_t u16_at(const uint4& v, int e) {
 
 __device__ __forceinline__ float bf16_at(const uint4& v, int e) { return __uint_as_float(u16_at(v, e) << 16); }
 
+// FP32-storage DSC stream: a slot's 8 values take two 16-byte loads.
+struct EntrySlot32 {
+    uint4 key, fl, val, val2;
+};
+
+__device__ __forceinline__ void load_slot(const uint16_t* key, const TcArgs& A, int base, EntrySlot32& s) {
+    s.key = __ldg(reinterpret_cast<const uint4*>(key + base));
+    s.fl = __ldg(reinterpret_cast<const uint4*>(A.fl + base));
+    const uint4* v = reinterpret_cast<const uint4*>(A.val32) + (base >> 2);
+    s.val = __ldg(v);
+    s.val2 = __ldg(v + 1);
+}
+
+__device__ __forceinline__ float slot_val(const EntrySlot& s, int e) { return bf16_at(s.val, e); }
+
+__device__ __forceinline__ float slot_val(const EntrySlot32& s, int e) {
+    const uint4& v = e < 4 ? s.val : s.val2;
+    const int i = e & 3;
+    return __uint_as_float(i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w);
+}
+
+// Value of stream entry j, read from memory (the tail of a run that leaves the warp).
+__device__ __forceinline__ float stream_val(const TcArgs& A, const EntrySlot&, int j) {
+    return __bfloat162float(A.val[j]);
+}
+
+__device__ __forceinline__ float stream_val(const TcArgs& A, const EntrySlot32&, int j) { return A.val32[j]; }
+
 __device__ __forceinline__ int chunk_beg(const TcArgs& A, int t, int c, int subs_per_chunk) {
     return A.sub_ptr[(int64_t)t * A.n_sub + (int64_t)c * subs_per_chunk];
 }
@@ -1051,14 +1121,29 @@ constexpr uint32_t DS_SBO = (DKC / 8) * 128;              // 8-row group stride 
 // device memory, read through L2).
 static __device__ __align__(128) uint4 g_zero_chunk[DS_BYTES / 16];
 
-__host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb) {
-    uint32_t d = (uint32_t)np * kp * 2;
+// Shared memory of a DSC CTA: D as an MMA operand (BF16 storage only: with FP32
+// storage D's two FP16 parts sit in tensor memory), the S stages (FP32 storage:
+// hi and lo parts), the brick weight table.
+__host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb, bool f32) {
+    uint32_t d = f32 ? 0u : (uint32_t)np * kp * 2;
     d = (d + 1023) / 1024 * 1024;
-    return d + DSTAGE * DS_BYTES + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) + 1024;
+    return d + DSTAGE * DS_BYTES * (f32 ? 2u : 1u) + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) + 1024;
 }
 
+// Tensor-memory columns of a DSC CTA: two 128-column accumulators (BF16 storage),
+// or D's FP16 hi and lo parts (kp/2 columns each) and one accumulator (FP32).
+__host__ __device__ inline uint32_t dsc_tmem_cols(int kp, bool f32) {
+    return (!f32 || kp + 128 <= 256) ? 256u : 512u;
+}
+
+// S[so] = s·ss as FP16; SPLIT (FP32 storage) also stores the FP16 rounding of
+// the remainder in the stage's second half, so that hi + lo carries 22 bits.
+template <bool SPLIT>
 __device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s, float ss) {
-    reinterpret_cast<__half*>(S)[so] = __float2half_rn(s * ss);
+    const float x = s * ss;
+    const __half h = __float2half_rn(x);
+    reinterpret_cast<__half*>(S)[so] = h;
+    if (SPLIT) reinterpret_cast<__half*>(S + DS_BYTES)[so] = __float2half_rn(x - __half2float(h));
 }
 
 // S[a, row] for the runs that start inside this slot (a run = entries with the
@@ -1072,8 +1157,8 @@ struct RunState {
     float cs, lead;
 };
 
-template <bool CHECK>
-__device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, int end, const float* wl,
+template <bool CHECK, bool SPLIT, class SlotT>
+__device__ __forceinline__ void dsc_runs(const SlotT& s, int base, int beg, int end, const float* wl,
                                          unsigned char* S, RunState& st, float ss) {
     // straight-line code: every lane does the same work for every entry
 #pragma unroll
@@ -1084,9 +1169,9 @@ __device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, 
             in = idx >= beg && idx < end;
         }
         const uint32_t f = u16_at(s.fl, e);
-        const float t = in ? bf16_at(s.val, e) * wl[f & 0x7FFFu] : 0.0f;
+        const float t = in ? slot_val(s, e) * wl[f & 0x7FFFu] : 0.0f;
         const bool head = in && !(f & CONT);
-        if (head && st.have) store_s(S, st.so, st.cs, ss);   // the previous run ends here
+        if (head && st.have) store_s<SPLIT>(S, st.so, st.cs, ss);   // the previous run ends here
         st.lead += (!st.have && !head) ? t : 0.0f;       // continuation of a run owned by the lane before
         st.cs = head ? t : st.cs + t;
         st.so = head ? u16_at(s.key, e) : st.so;
@@ -1095,11 +1180,12 @@ __device__ __forceinline__ void dsc_runs(const EntrySlot& s, int base, int beg, 
     st.head_seen = st.have;
 }
 
-__device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, int base, int beg, int end,
+template <bool SPLIT, class SlotT>
+__device__ __forceinline__ void dsc_slot(const TcArgs& A, const SlotT& s, int base, int beg, int end,
                                          const float* wl, unsigned char* S, int lane, float ss) {
     RunState st{false, false, 0u, 0.0f, 0.0f};
-    if (base >= beg && base + SLOT <= end) dsc_runs<false>(s, base, beg, end, wl, S, st, ss);
-    else dsc_runs<true>(s, base, beg, end, wl, S, st, ss);
+    if (base >= beg && base + SLOT <= end) dsc_runs<false, SPLIT>(s, base, beg, end, wl, S, st, ss);
+    else dsc_runs<true, SPLIT>(s, base, beg, end, wl, S, st, ss);
     // a run may pass through this whole slot into the one after it
     const int through = (!st.head_seen && base + SLOT < end) ? 1 : 0;
     const float nlead = __shfl_down_sync(0xffffffffu, st.lead, 1);
@@ -1113,11 +1199,11 @@ __device__ __forceinline__ void dsc_slot(const TcArgs& A, const EntrySlot& s, in
                 for (int j = j0; j < end; ++j) {
                     const uint32_t f = A.fl[j];
                     if (!(f & CONT)) break;
-                    st.cs += __bfloat162float(A.val[j]) * wl[f & 0x7FFFu];
+                    st.cs += stream_val(A, s, j) * wl[f & 0x7FFFu];
                 }
             }
         }
-        store_s(S, st.so, st.cs, ss);
+        store_s<SPLIT>(S, st.so, st.cs, ss);
     }
 }
 
@@ -1211,10 +1297,27 @@ __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
     return v;
 }
 
+// Bits of max |v| over n floats in global memory.
+__device__ __forceinline__ uint32_t f32_absmax_bits(const float* p, int n, int tid, int nthr) {
+    uint32_t m = 0u;
+    for (int i = tid; i < n; i += nthr) m = max(m, abs_bits(__ldg(p + i)));
+    return m;
+}
+
+// F32 = false: BF16 storage; S (A operand, 128 tile rows x K) and D (B operand)
+// in shared memory, Yᵀ[rows x θ] in one of two tensor-memory accumulators.
+// F32 = true: FP32 storage; D = D_hi + D_lo (FP16 parts of D·2^kD) is the A
+// operand in tensor memory (lane θ), S = S_hi + S_lo the B operand in shared
+// memory, Y[θ x rows] = D_hi·S_hi + D_hi·S_lo + D_lo·S_hi in one accumulator
+// (the dropped D_lo·S_lo is ~2^-22 of the product).
+template <bool F32>
 __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
+    using SlotT = typename std::conditional<F32, EntrySlot32, EntrySlot>::type;
+    constexpr uint32_t STG = F32 ? 2 * DS_BYTES : DS_BYTES;  // bytes of one S stage
+    constexpr uint32_t NACC = F32 ? 1 : 2;                    // accumulators in flight
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[DSTAGE], empty_bar[DSTAGE], zero_bar[DSTAGE], acc_full[2], acc_empty[2], fin_bar,
-        tab_bar;
+        tab_bar, d_ready;
     __shared__ uint32_t tmem_base, dmax_bits, xmax_bits;
     __shared__ int abort_flag, never;
     __shared__ int chunk_next[DSTAGE];  // next dynamically handed-out 256-entry block of the stage's chunk
@@ -1227,20 +1330,21 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t d_bytes = align_up((uint32_t)A.np * A.kp * 2, 1024);
+    const uint32_t d_bytes = F32 ? 0u : align_up((uint32_t)A.np * A.kp * 2, 1024);
     unsigned char* Ds = smem;
     unsigned char* Ss = smem + d_bytes;
-    float* wl = reinterpret_cast<float*>(Ss + DSTAGE * DS_BYTES);
+    float* wl = reinterpret_cast<float*>(Ss + DSTAGE * STG);
     const uint32_t SBO_D = (uint32_t)(A.kp / 8) * 128u;
 
-    // D as the B operand: rows θ (N), K = atoms; BF16 (its stored precision),
-    // zero-padded, then FP16 times 2^kD in place.
+    // BF16 storage: D as the B operand, rows θ (N), K = atoms; BF16 (its stored
+    // precision), zero-padded, then FP16 times 2^kD in place.
     if (tid == 0) dmax_bits = xmax_bits = 0u;
-    stage_d<false>(A, Ds, SBO_D, tid, blockDim.x);
+    if (!F32) stage_d<false>(A, Ds, SBO_D, tid, blockDim.x);
     __syncthreads();
     {
         // max |D| (for kD) and max |x| over the weight gather's block maxima (for kS)
-        uint32_t dm = warp_max_u32(bf16_absmax_bits(Ds, (uint32_t)A.np * A.kp, tid, blockDim.x));
+        uint32_t dm = F32 ? warp_max_u32(f32_absmax_bits(A.D, A.nt * A.na, tid, blockDim.x))
+                          : warp_max_u32(bf16_absmax_bits(Ds, (uint32_t)A.np * A.kp, tid, blockDim.x));
         uint32_t xm = 0u;
         for (int i = tid; i < A.n_xamax; i += blockDim.x) xm = max(xm, A.x_amax[i]);
         xm = warp_max_u32(xm);
@@ -1251,7 +1355,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     }
     __syncthreads();
     const int kD = f16_scale_exp(dmax_bits);
-    bf16_to_f16_scaled(Ds, (uint32_t)A.np * A.kp, kD, tid, blockDim.x);
+    if (!F32) bf16_to_f16_scaled(Ds, (uint32_t)A.np * A.kp, kD, tid, blockDim.x);
     // S = Σ_run val·x is stored as FP16 times 2^kS, with |S| <= run_vmax · max|x|
     int kS = 0;
     {
@@ -1277,12 +1381,14 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             mbar_init(&acc_empty[b], DSC_EPI_WARPS);
         }
         mbar_init(&fin_bar, 1);
+        mbar_init(&d_ready, DSC_EPI_WARPS);
         abort_flag = 0;
         never = 0;
         fence_barrier_init();
     }
+    const uint32_t tmem_cols = dsc_tmem_cols(A.kp, F32);
     if (warp == DSC_MMA_WARP) {
-        tmem_alloc(&tmem_base, 256);
+        tmem_alloc(&tmem_base, tmem_cols);
         tmem_relinquish();
     }
     fence_proxy_async_smem();
@@ -1304,7 +1410,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             int beg = chunk_beg(A, t, 0, spc), end = chunk_end(A, t, 0, spc, n_c);
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
-            EntrySlot cur{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+            SlotT cur{};
             if (have) load_slot(A.soff, A, base, cur);
             bool new_brick = true, dead = false;
             uint32_t cc = 0, tab_ph = 0, tab_n = 0;
@@ -1329,7 +1435,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     ++tab_n;
                 }
                 const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
-                unsigned char* S = Ss + st * DS_BYTES;
+                unsigned char* S = Ss + st * STG;
                 // the stage is free and cleared once the MMA thread's bulk zero copy lands
                 if (!dead && !warp_wait(&zero_bar[st], ph, &abort_flag)) {
                     abort_flag = 1;
@@ -1345,7 +1451,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 }
                 const int nbase = (nbeg & ~7) + tid * SLOT;
                 const bool nhave = nvalid && nbase < nend;
-                EntrySlot nxt{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+                SlotT nxt{};
                 bool pf = false;
                 // The chunk is cut into 256-entry blocks (one slot per lane): warp w
                 // takes block w, then blocks handed out by the stage's counter, so
@@ -1361,12 +1467,12 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     const bool more = bb + nb * (32 * SLOT) < end;  // warp-uniform
                     if (more) {
                         if (b2 < end) load_slot(A.soff, A, b2, nxt);
-                        else nxt = EntrySlot{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+                        else nxt = SlotT{};
                     } else if (nhave) {
                         load_slot(A.soff, A, nbase, nxt);
                         pf = true;
                     }
-                    dsc_slot(A, cur, base, beg, end, wl, S, lane, s_scale);
+                    dsc_slot<F32>(A, cur, base, beg, end, wl, S, lane, s_scale);
                     if (!more) break;
                     cur = nxt;
                     base = b2;
@@ -1402,6 +1508,37 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
         int cur_p = -1;  // batched launch: problem whose Σ out² is being accumulated
         if (A.bg.live && lane == 0 && A.partial)
             for (int p = 0; p < A.bg.n; ++p) A.partial[((int64_t)p * G + cta) * DSC_EPI_WARPS + q] = 0.0;
+        if constexpr (F32) {
+            // D·2^kD as FP16 hi and lo parts into tensor memory: lane θ = row, atom pairs
+            // along the columns, hi in [0, kp/2), lo in [kp/2, kp); zero-padded
+            const float sc = ldexpf(1.0f, kD);
+            const uint32_t ta = tb + ((uint32_t)(32 * q) << 16);
+            const int half = A.kp / 2;
+#pragma unroll 2
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                uint32_t rh[8], rl[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int a0 = 2 * (c0 + j);
+                    float d0 = 0.0f, d1 = 0.0f;
+                    if (row < A.nt) {
+                        if (a0 < A.na) d0 = __ldg(A.D + (int64_t)A.nt * a0 + row) * sc;
+                        if (a0 + 1 < A.na) d1 = __ldg(A.D + (int64_t)A.nt * (a0 + 1) + row) * sc;
+                    }
+                    const __half h0 = __float2half_rn(d0), h1 = __float2half_rn(d1);
+                    const __half2 hh = __halves2half2(h0, h1);
+                    const __half2 ll = __floats2half2_rn(d0 - __half2float(h0), d1 - __half2float(h1));
+                    rh[j] = *reinterpret_cast<const uint32_t*>(&hh);
+                    rl[j] = *reinterpret_cast<const uint32_t*>(&ll);
+                }
+                tmem_st8(ta + (uint32_t)c0, rh);
+                tmem_st8(ta + (uint32_t)(half + c0), rl);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&d_ready);
+        }
         for (int r = 0; !stop; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
@@ -1415,13 +1552,61 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 }
             }
             for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
-                const uint32_t ab = tcount & 1u, aph = (tcount >> 1) & 1u;
+                const uint32_t ab = tcount % NACC, aph = (tcount / NACC) & 1u;
+                int vj[4];  // F32: voxel of tile row 32·g + lane
+                if constexpr (F32) {
+                    // before the accumulator is ready: the tile's voxels, and its rows of b
+                    // into L2 (this thread's row), so that the loads below hit L2
+#pragma unroll
+                    for (int g4 = 0; g4 < 4; ++g4) vj[g4] = A.tile_vox[(int64_t)t * TILE_V + 32 * g4 + lane];
+                    const int vr = A.tile_vox[(int64_t)t * TILE_V + row];
+                    if (A.b && vr >= 0)
+                        for (int k = 0; k < A.nt; k += 32) prefetch_l2(A.b + (int64_t)A.nt * vr + k);
+                }
                 if (!warp_wait(&acc_full[ab], aph, &abort_flag)) {
                     abort_flag = 1;
                     stop = true;
                     break;
                 }
                 tc_fence_after();
+                if constexpr (F32) {
+                    // Y[θ, tile row]: this thread holds θ = row; 32 tile rows per load, their
+                    // voxels shuffled from the lanes that read them
+                    const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)A.kp;
+                    const bool th_ok = row < A.nt;
+                    float sqf = 0.0f;
+#pragma unroll
+                    for (int g4 = 0; g4 < 4; ++g4) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // 16 tile rows: their b values are loaded together, then combined
+                            uint32_t rr[16];
+                            float bv[16];
+                            tmem_ld16(taddr + (uint32_t)(32 * g4 + 16 * h), rr);
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int v = __shfl_sync(0xffffffffu, vj[g4], 16 * h + e);
+                                bv[e] = (A.b && v >= 0 && th_ok) ? __ldg(A.b + (int64_t)A.nt * v + row) : 0.0f;
+                            }
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int v = __shfl_sync(0xffffffffu, vj[g4], 16 * h + e);
+                                if (v >= 0 && th_ok) {
+                                    const float y = __uint_as_float(rr[e]) * y_unscale - bv[e];
+                                    if (wy) A.out[(int64_t)A.nt * v + row] = y;
+                                    sqf += y * y;
+                                }
+                            }
+                        }
+                    }
+                    sq += (double)sqf;
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[ab]);
+                    ++tcount;
+                    continue;
+                }
                 const int v = A.tile_vox[(int64_t)t * TILE_V + row];
                 const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + ab * 128u;
                 float sqf = 0.0f;
@@ -1487,7 +1672,68 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0) red[q] = sq;
         }
-    } else if (lane == 0) {
+    } else if (F32 && lane == 0) {
+        // ---------------- MMA issuer: Y[128 x 128] = D[θ x kp] · S (FP16 hi/lo operands)
+        const uint32_t idesc = idesc_f16_f32(128, TILE_V);
+        const uint32_t sS = smem_u32(Ss), half = (uint32_t)A.kp / 2, acc = tb + (uint32_t)A.kp;
+        uint32_t cc = 0, tcount = 0;
+        uint32_t zlast = 0;  // bit z: parity of the last zero-copy phase issued on stage z
+        bool stop = false;
+        for (int z = 0; z < DSTAGE; ++z) {  // clear both stages (hi and lo parts) for their first use
+            mbar_arrive_expect_tx(&zero_bar[z], STG);
+            bulk_copy_g2s(Ss + z * STG, g_zero_chunk, DS_BYTES, &zero_bar[z]);
+            bulk_copy_g2s(Ss + z * STG + DS_BYTES, g_zero_chunk, DS_BYTES, &zero_bar[z]);
+        }
+        // D's parts are in tensor memory once the four epilogue warps have stored theirs
+        if (!mbar_wait(&d_ready, 0, &abort_flag, WAIT_LIMIT)) {
+            abort_flag = 1;
+            stop = true;
+        }
+        tc_fence_after();
+        for (int r = 0; !stop; ++r) {
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1] && !stop; ++t) {
+                if (!mbar_wait(&acc_empty[0], (tcount & 1u) ^ 1u, &abort_flag, WAIT_LIMIT)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                for (int c = 0; c < n_c; ++c) {
+                    const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
+                    if (!mbar_wait(&full_bar[st], ph, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
+                    tc_fence_after();
+                    const uint32_t sb = sS + st * STG;
+#pragma unroll
+                    for (int kk = 0; kk < DKC / 16; ++kk) {
+                        const uint32_t ah = tb + (uint32_t)c * (DKC / 2) + kk * 8u;  // 16 atoms = 8 columns
+                        const uint64_t bh = smem_desc(sb + kk * 256u, 128u, DS_SBO);
+                        const uint64_t bl = smem_desc(sb + DS_BYTES + kk * 256u, 128u, DS_SBO);
+                        mma_f16_tmem_a(acc, ah, bh, idesc, (c | kk) != 0 ? 1u : 0u);
+                        mma_f16_tmem_a(acc, ah, bl, idesc, 1u);
+                        mma_f16_tmem_a(acc, ah + half, bh, idesc, 1u);
+                    }
+                    mma_commit(&empty_bar[st]);
+                    // once these MMAs have read the stage, clear it for its next use
+                    if (!mbar_wait(&empty_bar[st], ph, &abort_flag, WAIT_LIMIT)) { abort_flag = 1; stop = true; break; }
+                    chunk_next[st] = DSC_PROD_WARPS;  // published by the arrive below
+                    mbar_arrive_expect_tx(&zero_bar[st], STG);
+                    bulk_copy_g2s(Ss + st * STG, g_zero_chunk, DS_BYTES, &zero_bar[st]);
+                    bulk_copy_g2s(Ss + st * STG + DS_BYTES, g_zero_chunk, DS_BYTES, &zero_bar[st]);
+                    zlast ^= 1u << st;
+                    ++cc;
+                }
+                if (stop) break;
+                mma_commit(&acc_full[0]);
+                ++tcount;
+            }
+        }
+        mma_commit(&fin_bar);
+        if (!mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT)) abort_flag = 1;
+        for (int z = 0; z < DSTAGE; ++z)
+            if (!mbar_wait(&zero_bar[z], (zlast >> z) & 1u, &never, WAIT_LIMIT)) abort_flag = 1;
+    } else if (!F32 && lane == 0) {
         // ---------------- MMA issuer: Yᵀ[128 x np] = S[128 x kp] · Dᵀ (FP16 operands)
         const uint32_t idesc = idesc_f16_f32(128, (uint32_t)A.np);
         const uint32_t sS = smem_u32(Ss), sD = smem_u32(Ds);
@@ -1543,7 +1789,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
     if (warp == DSC_MMA_WARP) {
         tc_fence_after();
-        tmem_dealloc(tb, 256);
+        tmem_dealloc(tb, tmem_cols);
     }
     if (tid == 0 && A.partial && !A.bg.live && !abort_flag) {
         double tot = 0.0;
@@ -2086,8 +2332,13 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
     A.gate = gate;
     A.gate_mode = gate_mode;
     A.vec4 = (ix->nt % 4 == 0 && ((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) ? 1 : 0;
-    const uint32_t smem = dsc_smem_bytes(A.np, A.kp, A.max_fb);
     TileLayout& L = ix->tile;
+    const bool f32 = L.vbytes == 4;
+    if (f32) {
+        A.val = nullptr;
+        A.val32 = L.val.as<float>();
+    }
+    const uint32_t smem = dsc_smem_bytes(A.np, A.kp, A.max_fb, f32);
     const bool sparse = L.sparse && !bg.live && L.wb_total > 0 && L.n_nnz > 0;
     if (L.wb_total > 0) {
         if (sparse)
@@ -2107,11 +2358,12 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
         A.n_xamax = ix->num_sms * 8;
         LIFE_CHECK_LAUNCH();
     }
-    LIFE_CUDA_TRY(cudaFuncSetAttribute(dsc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = f32 ? dsc_tc_kernel<true> : dsc_tc_kernel<false>;
+    LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(ix->num_sms, L.n_bricks);
     if (n_partial) *n_partial = grid;
     if (!sparse) {
-        dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+        kern<<<grid, DSC_THREADS, smem, s>>>(A);
         LIFE_CHECK_LAUNCH();
         return LIFE_OK;
     }
@@ -2142,14 +2394,14 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
     }
     A.ctl = ctl;
     A.want_mode = DSC_MODE_FULL;
-    dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+    dsc_tc_kernel<false><<<grid, DSC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();
     A.want_mode = DSC_MODE_COMPACT;
     A.soff = L.c_soff.as<uint16_t>();
     A.fl = L.c_fl.as<uint16_t>();
     A.val = L.c_val.as<__nv_bfloat16>();
     A.chunk_end = L.c_chunk_end.as<int32_t>();
-    dsc_tc_kernel<<<grid, DSC_THREADS, smem, s>>>(A);
+    dsc_tc_kernel<false><<<grid, DSC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
