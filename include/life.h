@@ -53,7 +53,9 @@ enum { LIFE_LAYOUT_VOXEL = 0, LIFE_LAYOUT_FIBER = 1, LIFE_LAYOUT_ATOM = 2 };
 
 typedef struct {
     int32_t precision;     /* LIFE_FP32 (default) or LIFE_BF16 */
-    int32_t algo;          /* LIFE_ALGO_*: SIMT = CUDA-core kernels, TC = tensor-core kernels */
+    int32_t algo;          /* LIFE_ALGO_*: SIMT = CUDA-core kernels, TC = tensor-core kernels (BF16 storage:
+                              FP16 operands; FP32 storage: split FP16 hi/lo operands, Na <= 384);
+                              AUTO = TC for BF16 storage, SIMT for FP32 storage */
     int32_t brick_dim;     /* TC path: edge of the cubic voxel brick used for locality, 1..64 (0 = 8) */
     int32_t wc_groups;     /* TC path: WC scatter warp groups per tensor-memory lane quarter, 1, 2 or 4
                               (0 = 4, or the largest that fits in shared memory) */
@@ -172,11 +174,17 @@ LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, 
  * table slots non-zero) it streams only the live entries, rebuilding that stream
  * for w's support when it is stale or much larger than needed.  The result is
  * that of the full stream up to the association of FP32 run sums.
- * Precision on a TC index: Phi values and D are stored in BF16; the tensor cores
- * read D and S = Σ val·w as FP16 under exact power-of-two scales (D's from its
- * largest value, S's from max |w| and the largest run of Phi values), FP32
- * accumulation.  A run sum more than ~2^40 below the largest possible one in the
- * call underflows FP16 and contributes zero.
+ * Precision on a TC index with BF16 storage: Phi values and D are stored in BF16;
+ * the tensor cores read D and S = Σ val·w as FP16 under exact power-of-two scales
+ * (D's from its largest value, S's from max |w| and the largest run of Phi
+ * values), FP32 accumulation.  A run sum more than ~2^40 below the largest
+ * possible one in the call underflows FP16 and contributes zero.
+ * With FP32 storage (precision LIFE_FP32, algo LIFE_ALGO_TC; Na <= 384): Phi
+ * values stay FP32, S is summed in FP32, and D·2^kD and S·2^kS are each split into
+ * FP16 hi and lo parts; Y = D_hi·S_hi + D_hi·S_lo + D_lo·S_hi (FP32 accumulation)
+ * carries ~22 bits per product, relative error a few 1e-6 at Na = 360.  An
+ * infinite w or D gives a non-finite y where the exact y is non-finite, possibly
+ * NaN for ±inf (the two parts of the other operand can differ in sign).
  * Errors: LIFE_EINVAL when D, w or both y and sumsq are NULL.
  */
 LIFE_API life_status life_dsc(life_index idx, const float* D, const float* w, const float* b, float* y,
@@ -207,6 +215,11 @@ LIFE_API life_status life_index_sparse_stats(life_index idx, int64_t* out, void*
  * holding a NaN or inf of r is read unscaled, so there |r| > 65504 becomes inf);
  * the per-brick partial sums are 32-bit fixed point in a unit relative to the
  * brick's largest possible sum, FP32 where that bound is not a normal float.
+ * With FP32 storage: D and each tile of r are split into FP16 hi and lo parts
+ * under the same scales, Z = D_hi·R_hi + D_hi·R_lo + D_lo·R_hi per 128-atom block
+ * (FP32 accumulation), per-brick partial sums in FP32 (on the CUDA cores when D's
+ * parts and the Z slots do not fit tensor memory: ceil(Na/128)·ceil16(Nθ) > 320).
+ * Non-finite r as for DSC: non-finite g where the exact g is, ±inf possibly NaN.
  */
 LIFE_API life_status life_wc(life_index idx, const float* D, const float* r, float* g, double* sumsq,
                     void* stream);

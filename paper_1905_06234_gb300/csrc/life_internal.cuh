@@ -175,8 +175,10 @@ struct TileLayout {
     float run_vmax = 0.0f;   // largest Σ|val| (BF16 values) over one (atom, voxel) run of the DSC stream
     DevBuf x_amax;           // uint32 [num_sms·8] bits of max |x| per block of a DSC's weight gather
     DevBuf brick_cv;         // float [n_bricks]: (largest entry count of a fascicle) x (largest |val|)
-    DevBuf tile_amax;        // uint32 [n_tiles * 4]: bits of max |r| per tile row quarter (written by
-                             // every DSC that stores y, and by WC calls whose r did not come from one)
+    DevBuf tile_amax;        // uint32 [n_tiles * 4]: bits of |r| maxima, four slots per tile whose
+                             // maximum is the tile's max |r| (per row quarter from the BF16 DSC, per
+                             // θ quarter from the FP32 one, slot 0 from a WC's own pass); written by
+                             // every DSC that stores y, and by WC calls whose r did not come from one
 };
 
 // A block-diagonal index that concatenates several problems (batched solve):

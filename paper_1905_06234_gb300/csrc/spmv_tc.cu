@@ -476,10 +476,11 @@ __global__ void wc_key_kernel(const uint64_t* __restrict__ skey, int64_t m, int 
     }
 }
 
+template <class VT>
 __global__ void wc_stream_kernel(const uint64_t* __restrict__ key3, const uint32_t* __restrict__ pay3, int64_t m,
-                                 int bf, const uint16_t* __restrict__ fl, const __nv_bfloat16* __restrict__ val,
+                                 int bf, const uint16_t* __restrict__ fl, const VT* __restrict__ val,
                                  int32_t n_sub, int64_t n_segs, uint16_t* __restrict__ wkey, uint16_t* __restrict__ wfl,
-                                 __nv_bfloat16* __restrict__ wval, int32_t* __restrict__ wseg_ptr) {
+                                 VT* __restrict__ wval, int32_t* __restrict__ wseg_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = key3[j];
         const uint32_t src = pay3[j];
@@ -521,6 +522,10 @@ __global__ void run_vmax_kernel(const uint16_t* __restrict__ fl, const VT* __res
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
+
+// Tensor-memory columns the FP32-storage WC needs: D's FP16 hi and lo parts for
+// each 128-atom block (np/2 columns each) and three 64-column Z slots.
+__host__ __device__ inline int wc32_tmem_cols(int np, int kp) { return (kp / 128) * np + 3 * 64; }
 
 struct HostTiles {
     std::vector<int32_t> tile_vox, vox_tile, vox_row, tile_brick, brick_tile_ptr;
@@ -623,9 +628,12 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     }
     const int64_t m = ix->nnz;
     L.vbytes = ix->precision == LIFE_FP32 ? 4 : 2;
-    L.wc_stream = L.vbytes == 2;
     L.np = (ix->nt + 15) / 16 * 16;
     L.kp = (ix->na + 127) / 128 * 128;   // whole 128-atom DSC chunks
+    // the FP32-storage WC holds D's FP16 parts (np columns per 128-atom block) and a
+    // ring of three 64-column Z slots in tensor memory; beyond that WC runs on the
+    // CUDA cores
+    L.wc_stream = L.vbytes == 2 || wc32_tmem_cols(L.np, L.kp) <= 512;
     L.n_sub = L.kp / SUB;
     const int bf = ix->key_bits_f, ba = ix->key_bits_a, sa = bf, sv = bf + ba;
     std::vector<int32_t> ijk;
@@ -816,19 +824,25 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     if (L.wc_stream) {
         LIFE_TRY(L.wkey.alloc(sizeof(uint16_t) * m_pad));
         LIFE_TRY(L.wfl.alloc(sizeof(uint16_t) * m_pad));
-        LIFE_TRY(L.wval.alloc(sizeof(__nv_bfloat16) * m_pad));
+        LIFE_TRY(L.wval.alloc((size_t)L.vbytes * m_pad));
         LIFE_TRY(L.wseg_ptr.alloc(sizeof(int32_t) * (n_wsegs + 1)));
         LIFE_CUDA_TRY(cudaMemsetAsync(L.wkey.p, 0, sizeof(uint16_t) * m_pad, s));
         LIFE_CUDA_TRY(cudaMemsetAsync(L.wfl.p, 0, sizeof(uint16_t) * m_pad, s));
-        LIFE_CUDA_TRY(cudaMemsetAsync(L.wval.p, 0, sizeof(__nv_bfloat16) * m_pad, s));
+        LIFE_CUDA_TRY(cudaMemsetAsync(L.wval.p, 0, (size_t)L.vbytes * m_pad, s));
         if (m > 0) {
             wc_key_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), m, bf, key2.as<uint64_t>(), pay2.as<uint32_t>());
             LIFE_CHECK_LAUNCH();
             LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, nbits64(H.n_tiles) + 16 + bf, s));
-            wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
-                                                       L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub, n_wsegs,
-                                                       L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
-                                                       L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
+            if (L.vbytes == 4)
+                wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
+                                                           L.fl.as<uint16_t>(), L.val.as<float>(), L.n_sub, n_wsegs,
+                                                           L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
+                                                           L.wval.as<float>(), L.wseg_ptr.as<int32_t>());
+            else
+                wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
+                                                           L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub,
+                                                           n_wsegs, L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
+                                                           L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
             LIFE_CHECK_LAUNCH();
         } else {
             fill_kernel<<<grid1d(n_wsegs + 1), 256, 0, s>>>(L.wseg_ptr.as<int32_t>(), n_wsegs + 1, 0);
@@ -870,7 +884,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     }
     LIFE_TRY(L.brick_cv.alloc(sizeof(float) * std::max<int64_t>(H.n_bricks, 1)));
     LIFE_TRY(L.tile_amax.alloc(sizeof(uint32_t) * 4 * std::max<int64_t>(H.n_tiles, 1)));
-    if (H.n_bricks > 0 && L.wc_stream) {
+    if (H.n_bricks > 0 && L.wc_stream && L.vbytes == 2) {  // the FP32 WC sums in FP32 tables
         const int cv_smem = (int)sizeof(int32_t) * std::max(L.max_fb, 1);
         LIFE_CUDA_TRY(cudaFuncSetAttribute(brick_cv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cv_smem));
         brick_cv_kernel<<<(unsigned)std::min<int64_t>(H.n_bricks, 65535), 256, cv_smem, s>>>(
@@ -955,10 +969,11 @@ struct TcArgs {
     float* out;          // DSC: y (or NULL);   WC: g (zeroed by the caller)
     double* partial;     // DSC: per-CTA FP64 Σ out²
     const float* val32;  // DSC on an FP32-storage index: the stream's values (val is then unused)
+    const float* wval32; // WC on an FP32-storage index: the WC stream's values (wval is then unused)
     const float* wb;     // DSC: gathered brick weight tables
     const int32_t* wb_ptr;
     const float* brick_cv;    // WC: per-brick bound on Σ|val| of one fascicle
-    uint32_t* tile_amax;      // bits of max |r| per (tile, row quarter): written by DSC, read by WC
+    uint32_t* tile_amax;      // bits of |r| maxima, 4 slots per tile (their max is the tile's): DSC writes, WC reads
     const life_sbb_state* gate;
     int gate_mode;
     const uint32_t* x_amax;    // DSC: bits of max |x| per block of this call's weight gather
@@ -1136,14 +1151,30 @@ __host__ __device__ inline uint32_t dsc_tmem_cols(int kp, bool f32) {
     return (!f32 || kp + 128 <= 256) ? 256u : 512u;
 }
 
+// The FP16 remainder of x after its FP16 rounding h (hi + lo carries 22 bits);
+// zero where h is infinite, so that an infinite x stays infinite, not NaN.
+__device__ __forceinline__ float f16_rest(float x, __half h) {
+    const float hf = __half2float(h);
+    return isinf(hf) ? 0.0f : x - hf;
+}
+
+// hi = FP16(a), lo = FP16 of the remainder, for a pair (a, b).
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    const __half2 h2 = __halves2half2(ha, hb);
+    const __half2 l2 = __floats2half2_rn(f16_rest(a, ha), f16_rest(b, hb));
+    hi = *reinterpret_cast<const uint32_t*>(&h2);
+    lo = *reinterpret_cast<const uint32_t*>(&l2);
+}
+
 // S[so] = s·ss as FP16; SPLIT (FP32 storage) also stores the FP16 rounding of
-// the remainder in the stage's second half, so that hi + lo carries 22 bits.
+// the remainder in the stage's second half.
 template <bool SPLIT>
 __device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s, float ss) {
     const float x = s * ss;
     const __half h = __float2half_rn(x);
     reinterpret_cast<__half*>(S)[so] = h;
-    if (SPLIT) reinterpret_cast<__half*>(S + DS_BYTES)[so] = __float2half_rn(x - __half2float(h));
+    if (SPLIT) reinterpret_cast<__half*>(S + DS_BYTES)[so] = __float2half_rn(f16_rest(x, h));
 }
 
 // S[a, row] for the runs that start inside this slot (a run = entries with the
@@ -1525,11 +1556,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                         if (a0 < A.na) d0 = __ldg(A.D + (int64_t)A.nt * a0 + row) * sc;
                         if (a0 + 1 < A.na) d1 = __ldg(A.D + (int64_t)A.nt * (a0 + 1) + row) * sc;
                     }
-                    const __half h0 = __float2half_rn(d0), h1 = __float2half_rn(d1);
-                    const __half2 hh = __halves2half2(h0, h1);
-                    const __half2 ll = __floats2half2_rn(d0 - __half2float(h0), d1 - __half2float(h1));
-                    rh[j] = *reinterpret_cast<const uint32_t*>(&hh);
-                    rl[j] = *reinterpret_cast<const uint32_t*>(&ll);
+                    split_f16x2(d0, d1, rh[j], rl[j]);
                 }
                 tmem_st8(ta + (uint32_t)c0, rh);
                 tmem_st8(ta + (uint32_t)(half + c0), rl);
@@ -1575,6 +1602,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                     const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)A.kp;
                     const bool th_ok = row < A.nt;
                     float sqf = 0.0f;
+                    uint32_t am = 0u;  // bits of max |y| over this warp's θ and the tile's rows
 #pragma unroll
                     for (int g4 = 0; g4 < 4; ++g4) {
 #pragma unroll
@@ -1596,11 +1624,18 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                                     const float y = __uint_as_float(rr[e]) * y_unscale - bv[e];
                                     if (wy) A.out[(int64_t)A.nt * v + row] = y;
                                     sqf += y * y;
+                                    am = max(am, abs_bits(y));
                                 }
                             }
                         }
                     }
                     sq += (double)sqf;
+                    if (wy) {
+                        // slot q of the tile: max |y| over θ quarter q (the four slots of a
+                        // tile together hold its max, which is what a WC of y reads)
+                        am = warp_max_u32(am);
+                        if (lane == 0) A.tile_amax[(int64_t)t * 4 + q] = am;
+                    }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[ab]);
@@ -1819,11 +1854,15 @@ constexpr int ZW = 33;                                // row stride (floats) of 
 constexpr int ZSLOTS = 4;
 constexpr uint32_t ZW_BYTES = 32 * ZW * 4;
 
-__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups, int rbufs = 1) {
-    uint32_t d = (uint32_t)kp * np * 2;
+// Shared memory of a WC CTA: D as an MMA operand (BF16 storage; with FP32 storage
+// D's parts sit in tensor memory), the R tile buffers (FP32: hi and lo parts),
+// the scatter warps' Z tiles, the brick table.
+__host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, int wgroups, int rbufs = 1,
+                                                  bool f32 = false) {
+    uint32_t d = f32 ? 0u : (uint32_t)kp * np * 2;
     d = (d + 1023) / 1024 * 1024;
     uint32_t r = (uint32_t)TILE_V * np * 2;
-    r = (r + 1023) / 1024 * 1024;
+    r = (r + 1023) / 1024 * 1024 * (f32 ? 2u : 1u);
     return d + (uint32_t)rbufs * r + 4u * wgroups * ZW_BYTES + 4u * (uint32_t)(max_fb > 1 ? max_fb : 1) + 1024;
 }
 
@@ -2262,6 +2301,361 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
     }
 }
 
+// ------------------------------------------------------------ FP32-storage WC
+//
+// Z is computed transposed, Z[a, row] = Σθ D[θ, a]·r[θ, row] for each 128-atom
+// block of a tile: D = D_hi + D_lo (FP16 parts of D·2^kD) is the A operand in
+// tensor memory (lane = atom of the block, np/2 columns per part), the R tile
+// R_hi + R_lo (FP16 parts of r·2^kR) the B operand in shared memory, one half
+// tile (64 rows, N = 64) at a time: Z = D_hi·R_hi + D_hi·R_lo + D_lo·R_hi into
+// the next of three 64-column slots.  Scatter warp w reads tensor-memory lane
+// quarter w % 4, i.e. atoms 32·(w % 4) .. of every block, for the row quarters
+// h, h + wgroups, ... (h = w / 4), and adds val·Z into FP32 brick tables.
+
+constexpr int Z32_SLOTS = 3;
+
+template <bool CHECK>
+__device__ __forceinline__ void wc32_slot_t(const EntrySlot32& s, int base, int beg, int end, const float* Zw,
+                                            uint32_t gl_s, float sc) {
+#pragma unroll
+    for (int e = 0; e < SLOT; ++e) {
+        if (CHECK) {
+            const int idx = base + e;
+            if (idx < beg || idx >= end) continue;
+        }
+        const uint32_t k = u16_at(s.key, e);  // (row mod 32) | (atom mod 32) << 5
+        const float x = slot_val(s, e) * Zw[(k >> 5) * ZW + (k & 31u)] * sc;
+        red_add_shared_f32(gl_s + 4u * u16_at(s.fl, e), x);
+    }
+}
+
+__device__ __forceinline__ void wc32_load_slot(const TcArgs& A, int base, EntrySlot32& s) {
+    s.key = __ldg(reinterpret_cast<const uint4*>(A.wkey + base));
+    s.fl = __ldg(reinterpret_cast<const uint4*>(A.wfl + base));
+    const uint4* v = reinterpret_cast<const uint4*>(A.wval32) + (base >> 2);
+    s.val = __ldg(v);
+    s.val2 = __ldg(v + 1);
+}
+
+// Adds val·Z·sc for the entries [beg, end) of one WC segment (Zw[atom][row] holds
+// the segment's 32 x 32 block of Z); lane i takes entries 8i .. of each
+// 256-entry block, the next block loaded while the current one is processed.
+__device__ __forceinline__ void wc32_segment(const TcArgs& A, int beg, int end, const float* Zw, uint32_t gl_s,
+                                             float sc, int lane) {
+    int base = (beg & ~7) + lane * SLOT;
+    EntrySlot32 cur{};
+    if (base < end) wc32_load_slot(A, base, cur);
+    for (;;) {
+        const int nb = base + 32 * SLOT;
+        const bool more = __shfl_sync(0xffffffffu, nb, 0) < end;  // warp-uniform
+        EntrySlot32 nxt{};
+        if (more && nb < end) wc32_load_slot(A, nb, nxt);
+        if (base >= beg && base + SLOT <= end) wc32_slot_t<false>(cur, base, beg, end, Zw, gl_s, sc);
+        else wc32_slot_t<true>(cur, base, beg, end, Zw, gl_s, sc);
+        if (!more) break;
+        cur = nxt;
+        base = nb;
+    }
+}
+
+__global__ void __maxnreg__(96) wc_tc32_kernel(TcArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t r_full[2], r_empty[2], z_full[Z32_SLOTS], z_empty[Z32_SLOTS], fin_bar, d_ready;
+    __shared__ uint32_t tmem_base, dmax_bits;
+    __shared__ int abort_flag, never;
+    if (!A.bg.live && gate_skip(A.gate, A.gate_mode)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t r_part = align_up((uint32_t)TILE_V * A.np * 2, 1024), r_bytes = 2 * r_part;  // hi, lo
+    const int wg = A.wgroups, kc = A.kp / 128;
+    unsigned char* Rs = smem;  // A.rbufs tiles of r_bytes
+    float* Zc = reinterpret_cast<float*>(Rs + A.rbufs * r_bytes);
+    float* gl = Zc + 4 * wg * (ZW_BYTES / 4);
+    const uint32_t SBO_K = (uint32_t)(A.np / 8) * 128u;  // 8-row groups of the R tile (K = θ)
+    const uint32_t zb = (uint32_t)(kc * A.np);           // first column of the Z slots
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&r_full[b], WC_LOAD_WARPS);
+            mbar_init(&r_empty[b], 1);
+        }
+        for (int z = 0; z < Z32_SLOTS; ++z) {
+            mbar_init(&z_full[z], 1);
+            mbar_init(&z_empty[z], WC_SCAT_WARPS);
+        }
+        mbar_init(&fin_bar, 1);
+        mbar_init(&d_ready, 4 * kc);  // the warps that store D's blocks
+        abort_flag = 0;
+        never = 0;
+        dmax_bits = 0u;
+        fence_barrier_init();
+    }
+    if (warp == WC_MMA_WARP) {
+        tmem_alloc(&tmem_base, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = tmem_base;
+    const int G = gridDim.x, cta = blockIdx.x;
+    {
+        const uint32_t dm = warp_max_u32(f32_absmax_bits(A.D, A.nt * A.na, tid, blockDim.x));
+        if (lane == 0) atomicMax(&dmax_bits, dm);
+    }
+    __syncthreads();
+    const int kD = f16_scale_exp(dmax_bits);
+
+    if (warp < WC_SCAT_WARPS) {
+        const int q = warp & 3, h = warp >> 2;  // atoms 32q .. of each block; row quarters h, h + wg, ...
+        const bool active = h < wg;             // warps beyond wgroups groups only keep step
+        float* Zw = Zc + (active ? warp : 0) * (ZW_BYTES / 4);
+        const uint32_t gl_s = smem_u32(gl);
+        if (h < kc) {
+            // D·2^kD of block h (atoms 128h + 32q + lane) as FP16 hi and lo parts into
+            // this warp's lanes: θ pairs along the columns, zero-padded
+            const float sc = ldexpf(1.0f, kD);
+            const int a = 128 * h + 32 * q + lane, half = A.np / 2;
+            const uint32_t ta = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * A.np);
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                uint32_t rh[8], rl[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int t0 = 2 * (c0 + j);
+                    float d0 = 0.0f, d1 = 0.0f;
+                    if (a < A.na) {
+                        if (t0 < A.nt) d0 = __ldg(A.D + (int64_t)A.nt * a + t0) * sc;
+                        if (t0 + 1 < A.nt) d1 = __ldg(A.D + (int64_t)A.nt * a + t0 + 1) * sc;
+                    }
+                    split_f16x2(d0, d1, rh[j], rl[j]);
+                }
+                tmem_st8(ta + (uint32_t)c0, rh);
+                tmem_st8(ta + (uint32_t)(half + c0), rl);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&d_ready);
+        }
+        uint32_t kcount = 0;  // Z slots handed over so far (ring position)
+        bool dead = false;
+        for (int r = 0;; ++r) {
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
+            const int fb0 = A.brick_fasc_ptr[brick], nfb = A.brick_fasc_ptr[brick + 1] - fb0;
+            uint32_t am = 0u;
+            for (int i = 4 * A.brick_tile_ptr[brick] + lane; i < 4 * A.brick_tile_ptr[brick + 1]; i += 32)
+                am = max(am, A.tile_amax[i]);
+            am = warp_max_u32(am);
+            // Z in tensor memory is 2^(kR + kD)·Z (kR from the brick's max |r|, as the loader scales R)
+            const float sc = ldexpf(1.0f, -(f16_scale_exp(am) + kD));
+            for (int i = 32 * tid; i < nfb; i += 32 * WC_SCAT_THREADS) prefetch_l2(A.brick_fasc + fb0 + i);
+            if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
+            for (int i = tid; i < nfb; i += WC_SCAT_THREADS) gl[i] = 0.0f;
+            named_bar_sync(2, WC_SCAT_THREADS);
+            const int t0 = A.brick_tile_ptr[brick], t1 = A.brick_tile_ptr[brick + 1];
+            for (int t = t0; t < t1 && !dead; ++t) {
+                // segment bounds of the tile: lane i holds wseg(t, rq, i) for this warp's k-th row quarter rq
+                int bq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int rq = h + k * wg;
+                    bq[k] = (active && rq < 4 && lane <= A.n_sub) ? wseg(A, t, rq, lane) : 0;
+                }
+                for (int j = 0; j < kc && !dead; ++j) {
+                    for (int hh = 0; hh < 2 && !dead; ++hh, ++kcount) {
+                        // rows 64hh .. of atom block j sit in slot zs of the ring
+                        const uint32_t zs = kcount % Z32_SLOTS, zu = (kcount / Z32_SLOTS) & 1u;
+                        if (!warp_wait(&z_full[zs], zu, &abort_flag)) {
+                            abort_flag = 1;
+                            dead = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        if (active) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int rq = h + k * wg;
+                                if (rq >= 4 || (rq >> 1) != hh) continue;
+                                const int sub = 4 * j + q;
+                                const int beg = __shfl_sync(0xffffffffu, bq[k], sub);
+                                const int end = __shfl_sync(0xffffffffu, bq[k], sub + 1);
+                                if (beg >= end) continue;  // an empty segment needs no Z
+                                uint32_t rr[32];
+                                tmem_ld32(tb + ((uint32_t)(32 * q) << 16) + zb + zs * 64u + 32u * (uint32_t)(rq & 1),
+                                          rr);
+                                tmem_ld_wait();
+                                float* zrow = Zw + lane * ZW;  // this lane's atom, the row quarter's 32 rows
+#pragma unroll
+                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                                __syncwarp();
+                                wc32_segment(A, beg, end, Zw, gl_s, sc, lane);
+                                __syncwarp();
+                            }
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&z_empty[zs]);  // this warp is done with the slot
+                    }
+                }
+            }
+            if (named_bar_or(2, WC_SCAT_THREADS, dead || abort_flag != 0)) break;
+            flush_table(A.out, gl, A.brick_fasc + fb0, nfb, tid, WC_SCAT_THREADS);
+        }
+    } else if (warp < WC_MMA_WARP) {
+        // ---------------- R tile loader: r[:, v]·2^kR of the brick as FP16 hi and lo
+        // parts (rows = voxels, K = θ), kR as the scatter warps compute it
+        const int lt = tid - WC_SCAT_THREADS;
+        const int ngrp = A.np / 8;
+        const bool vec = A.vec4 != 0 && (A.nt % 8) == 0;
+        uint32_t tcount = 0;
+        bool stop = false;
+        for (int r = 0; !stop; ++r) {
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
+            int r_next = r + 1;
+            const int next_brick = live_brick(A, G, cta, r_next);
+            uint32_t am = 0u;
+            for (int i = 4 * A.brick_tile_ptr[brick] + lane; i < 4 * A.brick_tile_ptr[brick + 1]; i += 32)
+                am = max(am, A.tile_amax[i]);
+            const float rs = ldexpf(1.0f, f16_scale_exp(warp_max_u32(am)));
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1]; ++t) {
+                const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
+                unsigned char* Rb = Rs + rb * r_bytes;
+                if (!warp_wait(&r_empty[rb], (rk & 1u) ^ 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                const int total = TILE_V * ngrp;
+                for (int u0 = lt; u0 < total; u0 += 2 * WC_LOAD_THREADS) {
+                    float4 lo[2], hi[2];
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const int u = u0 + s2 * WC_LOAD_THREADS;
+                        lo[s2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        hi[s2] = lo[s2];
+                        if (u < total) {
+                            const int row = u / ngrp, g8 = u % ngrp;
+                            const int v = A.tile_vox[(int64_t)t * TILE_V + row];
+                            if (v >= 0) {
+                                const float* src = A.x + (int64_t)A.nt * v + 8 * g8;
+                                if (vec && 8 * g8 + 8 <= A.nt) {
+                                    lo[s2] = __ldg(reinterpret_cast<const float4*>(src));
+                                    hi[s2] = __ldg(reinterpret_cast<const float4*>(src) + 1);
+                                } else {
+                                    float e[8];
+#pragma unroll
+                                    for (int z = 0; z < 8; ++z) e[z] = (8 * g8 + z < A.nt) ? src[z] : 0.0f;
+                                    lo[s2] = make_float4(e[0], e[1], e[2], e[3]);
+                                    hi[s2] = make_float4(e[4], e[5], e[6], e[7]);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const int u = u0 + s2 * WC_LOAD_THREADS;
+                        if (u >= total) continue;
+                        const int row = u / ngrp, g8 = u % ngrp;
+                        uint4 ph, pl;
+                        split_f16x2(lo[s2].x * rs, lo[s2].y * rs, ph.x, pl.x);
+                        split_f16x2(lo[s2].z * rs, lo[s2].w * rs, ph.y, pl.y);
+                        split_f16x2(hi[s2].x * rs, hi[s2].y * rs, ph.z, pl.z);
+                        split_f16x2(hi[s2].z * rs, hi[s2].w * rs, ph.w, pl.w);
+                        const uint32_t off = kmajor_off(row, 8 * g8, SBO_K);
+                        *reinterpret_cast<uint4*>(Rb + off) = ph;
+                        *reinterpret_cast<uint4*>(Rb + r_part + off) = pl;
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&r_full[rb]);
+                ++tcount;
+                // pull the voxel rows of r of the tile A.rbufs ahead into L2
+                int tn = t + A.rbufs;
+                if (tn >= A.brick_tile_ptr[brick + 1]) {
+                    tn -= A.brick_tile_ptr[brick + 1];
+                    tn = (next_brick >= 0 && A.brick_tile_ptr[next_brick] + tn < A.brick_tile_ptr[next_brick + 1])
+                             ? A.brick_tile_ptr[next_brick] + tn : -1;
+                }
+                if (tn >= 0) {
+                    const int32_t* tvn = A.tile_vox + (int64_t)tn * TILE_V;
+                    for (int row = lt; row < TILE_V; row += WC_LOAD_THREADS) {
+                        const int v = __ldg(tvn + row);
+                        if (v < 0) continue;
+                        const char* a = reinterpret_cast<const char*>(A.x + (int64_t)A.nt * v);
+                        const char* e = a + 4 * A.nt - 1;
+                        for (const char* c = a; c < e; c += 128) prefetch_l2(c);
+                        prefetch_l2(e);
+                    }
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer: Z[128 atoms x 64 rows] = D_blk · R_half for each
+        // 128-atom block and half tile, into the next slot of the tensor-memory ring
+        const uint32_t idesc = idesc_f16_f32(128, 64);
+        const uint32_t sR0 = smem_u32(Rs), half = (uint32_t)A.np / 2;
+        uint32_t tcount = 0, kcount = 0;
+        bool stop = false;
+        // D's parts are in tensor memory once the warps that store them have arrived
+        if (!mbar_wait(&d_ready, 0, &abort_flag, WAIT_LIMIT)) {
+            abort_flag = 1;
+            stop = true;
+        }
+        tc_fence_after();
+        for (int r = 0; !stop; ++r) {
+            const int brick = live_brick(A, G, cta, r);
+            if (brick < 0) break;
+            for (int t = A.brick_tile_ptr[brick]; t < A.brick_tile_ptr[brick + 1] && !stop; ++t) {
+                const uint32_t rb = A.rbufs == 2 ? (tcount & 1u) : 0u, rk = A.rbufs == 2 ? (tcount >> 1) : tcount;
+                const uint32_t sR = sR0 + rb * r_bytes;
+                if (!mbar_wait(&r_full[rb], rk & 1u, &abort_flag, WAIT_LIMIT)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                for (int j = 0; j < kc && !stop; ++j) {
+                    for (int hh = 0; hh < 2; ++hh, ++kcount) {
+                        const uint32_t zs = kcount % Z32_SLOTS, zu = (kcount / Z32_SLOTS) & 1u;
+                        if (!mbar_wait(&z_empty[zs], zu ^ 1u, &abort_flag, WAIT_LIMIT)) {  // the slot was read
+                            abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t zt = tb + zb + zs * 64u;
+                        const uint32_t sb = sR + (uint32_t)(8 * hh) * SBO_K;  // rows 64hh .. 64hh + 63
+                        for (int kk = 0; kk < A.np / 16; ++kk) {
+                            const uint32_t ah = tb + (uint32_t)(j * A.np) + kk * 8u;  // 16 θ = 8 columns
+                            const uint64_t bh = smem_desc(sb + kk * 256u, 128u, SBO_K);
+                            const uint64_t bl = smem_desc(sb + r_part + kk * 256u, 128u, SBO_K);
+                            mma_f16_tmem_a(zt, ah, bh, idesc, kk != 0 ? 1u : 0u);
+                            mma_f16_tmem_a(zt, ah, bl, idesc, 1u);
+                            mma_f16_tmem_a(zt, ah + half, bh, idesc, 1u);
+                        }
+                        mma_commit(&z_full[zs]);
+                    }
+                }
+                if (stop) break;
+                mma_commit(&r_empty[rb]);
+                ++tcount;
+            }
+        }
+        mma_commit(&fin_bar);
+        if (!mbar_wait(&fin_bar, 0, &never, WAIT_LIMIT)) abort_flag = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(A.status, DEV_TIMEOUT);
+    if (warp == WC_MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tb, 512);
+    }
+}
+
 // ============================================================== launchers
 
 // WC scatter groups for the next launch: the requested number (4 by default),
@@ -2271,7 +2665,7 @@ int wc_effective_groups(const life_index_s* ix) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device) != cudaSuccess) return 0;
     const TileLayout& L = ix->tile;
     int wg = ix->wc_groups > 0 ? ix->wc_groups : 4;
-    while (wg >= 1 && wc_smem_bytes(L.np, L.kp, L.max_fb, wg) + 256 > (uint32_t)optin) wg /= 2;
+    while (wg >= 1 && wc_smem_bytes(L.np, L.kp, L.max_fb, wg, 1, L.vbytes == 4) + 256 > (uint32_t)optin) wg /= 2;
     return wg;
 }
 
@@ -2280,7 +2674,7 @@ static int wc_r_buffers(const life_index_s* ix, int wg) {
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device) != cudaSuccess) return 1;
     const TileLayout& L = ix->tile;
-    return wc_smem_bytes(L.np, L.kp, L.max_fb, wg, 2) + 256 <= (uint32_t)optin ? 2 : 1;
+    return wc_smem_bytes(L.np, L.kp, L.max_fb, wg, 2, L.vbytes == 4) + 256 <= (uint32_t)optin ? 2 : 1;
 }
 
 static TcArgs make_args(life_index_s* ix) {
@@ -2423,18 +2817,24 @@ life_status wc_tc(life_index_s* ix, const float* D, const float* r, float* g, co
     A.wgroups = wc_effective_groups(ix);
     if (A.wgroups < 1) {
         set_error("wc_tc: %u bytes of shared memory needed even with one scatter group",
-                  wc_smem_bytes(A.np, A.kp, A.max_fb, 1));
+                  wc_smem_bytes(A.np, A.kp, A.max_fb, 1, 1, ix->tile.vbytes == 4));
         return LIFE_ENOTSUP;
     }
     A.rbufs = wc_r_buffers(ix, A.wgroups);
-    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups, A.rbufs);
-    LIFE_CUDA_TRY(cudaFuncSetAttribute(wc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool f32 = ix->tile.vbytes == 4;
+    if (f32) {
+        A.wval = nullptr;
+        A.wval32 = ix->tile.wval.as<float>();
+    }
+    const uint32_t smem = wc_smem_bytes(A.np, A.kp, A.max_fb, A.wgroups, A.rbufs, f32);
+    auto kern = f32 ? wc_tc32_kernel : wc_tc_kernel;
+    LIFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ix->tile.n_tiles > 0 && !r_is_dsc_out) {
         wc_amax_kernel<<<(unsigned)std::min<int64_t>(ix->tile.n_tiles, (int64_t)ix->num_sms * 8), AMAX_THREADS, 0, s>>>(A);
         LIFE_CHECK_LAUNCH();
     }
     const int grid = (int)std::min<int64_t>(ix->num_sms, ix->tile.n_bricks);
-    wc_tc_kernel<<<grid, WC_THREADS, smem, s>>>(A);
+    kern<<<grid, WC_THREADS, smem, s>>>(A);
     LIFE_CHECK_LAUNCH();
     return LIFE_OK;
 }
