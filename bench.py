@@ -384,11 +384,12 @@ def sparse_dsc_sweep(life, live, full, fracs=(0.0, 0.5, 0.9, 0.97), reps=10):
     return out
 
 
-def time_to_tolerance(life, lo, hi, tol, switches=(1e-3, 3e-4, 1e-4), max_iter=500):
+def time_to_tolerance(life, lo, hi, tol, switches=(1e-3, 3e-4, 1e-4), max_iter=500, hi_tc=None):
     """Time to ‖g~‖ <= tol·‖g~_0‖ from w = 1: the plain path `hi` alone, the fast
     path `lo` alone, and `lo` until each switch tolerance followed by `hi` to tol
     from the same w and state (the state keeps ‖g~_0‖, so both phases test against
-    the same reference).  Graphs are built by untimed calls first."""
+    the same reference); with `hi_tc` (FP32 storage on the tensor cores) also that
+    path alone and as the second phase.  Graphs are built by untimed calls first."""
     import torch
     s = torch.cuda.current_stream()
 
@@ -406,7 +407,8 @@ def time_to_tolerance(life, lo, hi, tol, switches=(1e-3, 3e-4, 1e-4), max_iter=5
                 "rel_pg": (x["gg"] / x["gg0"]) ** 0.5 if x["gg0"] > 0 else None}
 
     out = {"tol": tol, "max_iter": max_iter}
-    for name, path in (("plain", hi), ("fast", lo)):
+    alone = [("plain", hi), ("fast", lo)] + ([("fp32_tc", hi_tc)] if hi_tc is not None else [])
+    for name, path in alone:
         path.reset()
         life.life_sbbnnls_solve(path.idx, path.D, path.b, path.w, 1, path.st, path.ws, tol=tol)
         torch.cuda.synchronize()
@@ -415,29 +417,42 @@ def time_to_tolerance(life, lo, hi, tol, switches=(1e-3, 3e-4, 1e-4), max_iter=5
                                                   tol=tol))
         out[name] = dict(state(path.st), s=t)
 
-    out["fast_then_plain"] = {}
-    for tol_lo in switches:
-        def mixed():
-            life.life_sbbnnls_solve(lo.idx, lo.D, lo.b, lo.w, max_iter, lo.st, lo.ws, tol=tol_lo)
-            ph1 = life.read_sbb_state(lo.st)["it"] if timing_phase1 else None
-            life.life_sbb_state_resume(lo.st)
-            life.life_sbbnnls_solve(hi.idx, hi.D, hi.b, lo.w, max_iter, lo.st, hi.ws, tol=tol)
-            return ph1
+    seconds = [("fast_then_plain", hi)] + ([("fast_then_fp32_tc", hi_tc)] if hi_tc is not None else [])
+    for key, second in seconds:
+        out[key] = {}
+        for tol_lo in switches:
+            def mixed():
+                life.life_sbbnnls_solve(lo.idx, lo.D, lo.b, lo.w, max_iter, lo.st, lo.ws, tol=tol_lo)
+                ph1 = life.read_sbb_state(lo.st)["it"] if timing_phase1 else None
+                life.life_sbb_state_resume(lo.st)
+                life.life_sbbnnls_solve(second.idx, second.D, second.b, lo.w, max_iter, lo.st, second.ws, tol=tol)
+                return ph1
 
-        timing_phase1 = True
-        lo.reset()
-        it_fast = mixed()
-        torch.cuda.synchronize()
-        timing_phase1 = False
-        lo.reset()
-        t = timed(mixed)
-        row = dict(state(lo.st), s=t, iters_fast=int(it_fast))
-        out["fast_then_plain"][f"{tol_lo:g}"] = row
+            timing_phase1 = True
+            lo.reset()
+            it_fast = mixed()
+            torch.cuda.synchronize()
+            timing_phase1 = False
+            lo.reset()
+            t = timed(mixed)
+            out[key][f"{tol_lo:g}"] = dict(state(lo.st), s=t, iters_fast=int(it_fast))
     done = {k: v for k, v in out["fast_then_plain"].items() if v["converged"]}
     if out["plain"]["converged"] and done:
         best = min(done, key=lambda k: done[k]["s"])
         out["best_switch"] = best
         out["speedup_at_tol"] = out["plain"]["s"] / done[best]["s"]
+    # the fastest route to the tolerance among all forms, against the plain FP32 solve
+    routes = {}
+    if out.get("fp32_tc", {}).get("converged"):
+        routes["fp32_tc"] = out["fp32_tc"]["s"]
+    for key, _ in seconds:
+        for sw, v in out[key].items():
+            if v["converged"]:
+                routes[f"{key}@{sw}"] = v["s"]
+    if out["plain"]["converged"] and routes:
+        best = min(routes, key=routes.get)
+        out["best_route"] = best
+        out["best_route_speedup"] = out["plain"]["s"] / routes[best]
     return out
 
 
@@ -445,10 +460,11 @@ def run_batched(life, D, max_iter=500, tol=1e-4, tol_switch=1e-3):
     """The batched workload: 16 independent problems of uneven size (Nf log-uniform
     in 1e4..2e5, cubic grids of edge 32..80, no mask) solved by SBB-NNLS to
     ‖g~‖/‖g~_0‖ <= tol, as one batched solve (one graph launch) and as 16
-    sequential plain solves, for the FP32 CUDA-core and BF16 tensor-core paths,
-    and as BF16 batched iterations to tol_switch followed by FP32 batched
-    iterations to tol from the same weights and states.  The BF16 batch's tile
-    layout comes from the autotuner."""
+    sequential plain solves, for the FP32 CUDA-core, FP32 tensor-core and BF16
+    tensor-core paths, and as BF16 batched iterations to tol_switch followed by
+    FP32 batched iterations (CUDA cores or tensor cores) to tol from the same
+    weights and states.  The tensor-core batches' tile layouts come from the
+    autotuner."""
     import torch
     import synth
     t0 = time.time()
@@ -463,6 +479,7 @@ def run_batched(life, D, max_iter=500, tol=1e-4, tol_switch=1e-3):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     batches, all_idxs = {}, []
     for name, prec, algo in (("fp32-simt", life.LIFE_FP32, life.LIFE_ALGO_SIMT),
+                             ("fp32-tc", life.LIFE_FP32, life.LIFE_ALGO_TC),
                              ("bf16-tc", life.LIFE_BF16, life.LIFE_ALGO_TC)):
         idxs = [life.upload_problem(p, precision=prec, algo=algo) for p in probs]
         all_idxs += idxs
@@ -518,34 +535,36 @@ def run_batched(life, D, max_iter=500, tol=1e-4, tol_switch=1e-3):
                      "final_obj": [x["obj"] for x in bst],
                      "max_rel_obj_diff_vs_sequential": obj_dev, "create_s": create_s, "batch": batch.info()}
         del seq
-    # BF16 batched iterations to tol_switch, then FP32 batched iterations to tol,
-    # from the same weights and states (both graphs built by an untimed run)
-    ws = [torch.ones(p.n_fasc, device=dev) for p in probs]
-    st = life.new_batch_states(len(probs))
-    wlo, whi = life.new_batch_workspace(batches["bf16-tc"]), life.new_batch_workspace(batches["fp32-simt"])
+    # BF16 batched iterations to tol_switch, then FP32 batched iterations to tol (on
+    # the CUDA cores or the tensor cores), from the same weights and states (both
+    # graphs built by an untimed run)
+    for hi_name in ("fp32-simt", "fp32-tc"):
+        ws = [torch.ones(p.n_fasc, device=dev) for p in probs]
+        st = life.new_batch_states(len(probs))
+        wlo, whi = life.new_batch_workspace(batches["bf16-tc"]), life.new_batch_workspace(batches[hi_name])
 
-    def mixed():
-        life.life_batch_solve(batches["bf16-tc"], D, bs, ws, max_iter, st, wlo, tol=tol_switch)
-        life.life_sbb_state_resume(st, len(probs))
-        life.life_batch_solve(batches["fp32-simt"], D, bs, ws, max_iter, st, whi, tol=tol)
+        def mixed():
+            life.life_batch_solve(batches["bf16-tc"], D, bs, ws, max_iter, st, wlo, tol=tol_switch)
+            life.life_sbb_state_resume(st, len(probs))
+            life.life_batch_solve(batches[hi_name], D, bs, ws, max_iter, st, whi, tol=tol)
 
-    mixed()
-    torch.cuda.synchronize()
-    for w in ws:
-        w.fill_(1.0)
-    st.copy_(life.new_batch_states(len(probs)))
-    e0.record(s)
-    mixed()
-    e1.record(s)
-    torch.cuda.synchronize()
-    t_mix = e0.elapsed_time(e1) / 1e3
-    mst = life.read_batch_states(st, len(probs))
-    out["bf16-tc+fp32-simt"] = {"batched_ms": t_mix * 1e3, "tol_switch": tol_switch,
-                                "iters": [int(x["it"]) for x in mst],
-                                "converged": int(sum(x["converged"] for x in mst)),
-                                "final_obj": [x["obj"] for x in mst],
-                                "speedup_vs_fp32_sequential": out["fp32-simt"]["sequential_ms"] / (t_mix * 1e3),
-                                "speedup_vs_fp32_batched": out["fp32-simt"]["batched_ms"] / (t_mix * 1e3)}
+        mixed()
+        torch.cuda.synchronize()
+        for w in ws:
+            w.fill_(1.0)
+        st.copy_(life.new_batch_states(len(probs)))
+        e0.record(s)
+        mixed()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_mix = e0.elapsed_time(e1) / 1e3
+        mst = life.read_batch_states(st, len(probs))
+        out["bf16-tc+" + hi_name] = {"batched_ms": t_mix * 1e3, "tol_switch": tol_switch,
+                                     "iters": [int(x["it"]) for x in mst],
+                                     "converged": int(sum(x["converged"] for x in mst)),
+                                     "final_obj": [x["obj"] for x in mst],
+                                     "speedup_vs_fp32_sequential": out["fp32-simt"]["sequential_ms"] / (t_mix * 1e3),
+                                     "speedup_vs_fp32_batched": out["fp32-simt"]["batched_ms"] / (t_mix * 1e3)}
     for b_ in batches.values():
         b_.close()
     for ix in all_idxs:
@@ -580,6 +599,14 @@ def run_ours(args):
     b += torch.from_numpy(p.noise).to(dev)
     fp32.b = b
     paths = {"fp32-simt": fp32}
+    if args.precision in ("fp32", "both"):
+        # FP32 storage on the tensor cores (split FP16 hi/lo operands)
+        try:
+            paths["fp32-tc"] = GpuPath(life, p, D, b, life.LIFE_FP32, life.LIFE_ALGO_TC, autotune=args.autotune)
+        except life.LifeError as e:
+            paths["fp32-tc"] = None
+            if rank == 0:
+                print(f"# fp32 tensor-core path unavailable: {e}", file=sys.stderr)
     if args.precision in ("bf16", "both"):
         try:
             paths["bf16-tc"] = GpuPath(life, p, D, b, life.LIFE_BF16, life.LIFE_ALGO_TC, autotune=args.autotune)
@@ -640,7 +667,8 @@ def run_ours(args):
             solves["bf16-tc-live"] = full_solve(life, live_path)
             solves["bf16-tc-live"]["dsc_vs_zero_weights"] = sparse_dsc_sweep(life, live_path, paths["bf16-tc"])
         if paths.get("bf16-tc") is not None:
-            tol_run = time_to_tolerance(life, paths["bf16-tc"], paths["fp32-simt"], tol=1e-4)
+            tol_run = time_to_tolerance(life, paths["bf16-tc"], paths["fp32-simt"], tol=1e-4,
+                                        hi_tc=paths.get("fp32-tc"))
     batched = run_batched(life, D) if args.batched == "on" else None
     if rank != 0:
         if dist:
@@ -677,6 +705,9 @@ def run_ours(args):
                       "wc_ms": v["kern"]["wc_s"] * 1e3,
                       "dsc_gbs": v["kern"]["dsc_bytes"] / v["kern"]["dsc_s"] / 1e9,
                       "wc_gbs": v["kern"]["wc_bytes"] / v["kern"]["wc_s"] / 1e9,
+                      "dsc_frac": v["kern"]["dsc_bytes"] / v["kern"]["dsc_s"] / 1e9 / peak,
+                      "wc_frac": v["kern"]["wc_bytes"] / v["kern"]["wc_s"] / 1e9 / peak,
+                      "vs_fp32_simt": results["fp32-simt"]["dt"] / v["dt"],
                       "index_build_s": v["path"].build_s} for k, v in results.items()},
         "vs_plain_fp32": (args.steps / best["dt"]) / (args.steps / results["fp32-simt"]["dt"]),
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",

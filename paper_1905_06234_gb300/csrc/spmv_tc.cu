@@ -1136,13 +1136,18 @@ constexpr uint32_t DS_SBO = (DKC / 8) * 128;              // 8-row group stride 
 // device memory, read through L2).
 static __device__ __align__(128) uint4 g_zero_chunk[DS_BYTES / 16];
 
+// FP32 storage: each epilogue warp transposes its 32 x 32 blocks of Y through a
+// padded shared-memory tile.
+constexpr uint32_t DSC_TW = 33;  // row stride (floats) of an epilogue warp's transpose tile
+
 // Shared memory of a DSC CTA: D as an MMA operand (BF16 storage only: with FP32
 // storage D's two FP16 parts sit in tensor memory), the S stages (FP32 storage:
-// hi and lo parts), the brick weight table.
+// hi and lo parts), the brick weight table, and (FP32) the epilogue's transpose tiles.
 __host__ __device__ inline uint32_t dsc_smem_bytes(int np, int kp, int max_fb, bool f32) {
     uint32_t d = f32 ? 0u : (uint32_t)np * kp * 2;
     d = (d + 1023) / 1024 * 1024;
-    return d + DSTAGE * DS_BYTES * (f32 ? 2u : 1u) + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) + 1024;
+    return d + DSTAGE * DS_BYTES * (f32 ? 2u : 1u) + 4u * (uint32_t)((max_fb + 3) / 4 * 4 + 4) +
+           (f32 ? 4u * DSC_EPI_WARPS * 32u * DSC_TW : 0u) + 1024;
 }
 
 // Tensor-memory columns of a DSC CTA: two 128-column accumulators (BF16 storage),
@@ -1365,6 +1370,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     unsigned char* Ds = smem;
     unsigned char* Ss = smem + d_bytes;
     float* wl = reinterpret_cast<float*>(Ss + DSTAGE * STG);
+    float* Ts = wl + ((A.max_fb + 3) / 4 * 4 + 4);  // F32: the epilogue warps' transpose tiles
     const uint32_t SBO_D = (uint32_t)(A.kp / 8) * 128u;
 
     // BF16 storage: D as the B operand, rows θ (N), K = atoms; BF16 (its stored
@@ -1412,7 +1418,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             mbar_init(&acc_empty[b], DSC_EPI_WARPS);
         }
         mbar_init(&fin_bar, 1);
-        mbar_init(&d_ready, DSC_EPI_WARPS);
+        mbar_init(&d_ready, DSC_MMA_WARP);  // every producer and epilogue warp stores part of D
         abort_flag = 0;
         never = 0;
         fence_barrier_init();
@@ -1432,6 +1438,33 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     const int spc = DKC / SUB;  // sub-chunks per chunk
     double sq = 0.0;
 
+    if (F32 && warp < DSC_MMA_WARP) {
+        // D·2^kD as FP16 hi and lo parts into tensor memory (lane θ, atom pairs along
+        // the columns, hi in [0, kp/2), lo in [kp/2, kp), zero-padded), shared by the
+        // producer and epilogue warps: each writes its lane quarter warp % 4, taking
+        // every n-th group of 16 columns among the warps of that quarter
+        const int q4 = warp & 3, rank = warp >> 2, nwq = (DSC_MMA_WARP - 1 - q4) / 4 + 1;
+        const int th = 32 * q4 + lane, half = A.kp / 2;
+        const float sc = ldexpf(1.0f, kD);
+        const uint32_t ta = tb + ((uint32_t)(32 * q4) << 16);
+        for (int c0 = 16 * rank; c0 < half; c0 += 16 * nwq) {
+            float d[32];  // loads first: the stores below stay ordered with memory accesses
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int a0 = 2 * c0 + j;
+                d[j] = (th < A.nt && a0 < A.na) ? __ldg(A.D + (int64_t)A.nt * a0 + th) * sc : 0.0f;
+            }
+            uint32_t rh[16], rl[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) split_f16x2(d[2 * j], d[2 * j + 1], rh[j], rl[j]);
+            tmem_st16(ta + (uint32_t)c0, rh);
+            tmem_st16(ta + (uint32_t)(half + c0), rl);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d_ready);
+    }
     if (warp < DSC_PROD_WARPS) {
         // ---------------- producers: S[a, row] = Σ val·w for one 128-atom chunk
         int r = 0;
@@ -1539,33 +1572,6 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
         int cur_p = -1;  // batched launch: problem whose Σ out² is being accumulated
         if (A.bg.live && lane == 0 && A.partial)
             for (int p = 0; p < A.bg.n; ++p) A.partial[((int64_t)p * G + cta) * DSC_EPI_WARPS + q] = 0.0;
-        if constexpr (F32) {
-            // D·2^kD as FP16 hi and lo parts into tensor memory: lane θ = row, atom pairs
-            // along the columns, hi in [0, kp/2), lo in [kp/2, kp); zero-padded
-            const float sc = ldexpf(1.0f, kD);
-            const uint32_t ta = tb + ((uint32_t)(32 * q) << 16);
-            const int half = A.kp / 2;
-#pragma unroll 2
-            for (int c0 = 0; c0 < half; c0 += 8) {
-                uint32_t rh[8], rl[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int a0 = 2 * (c0 + j);
-                    float d0 = 0.0f, d1 = 0.0f;
-                    if (row < A.nt) {
-                        if (a0 < A.na) d0 = __ldg(A.D + (int64_t)A.nt * a0 + row) * sc;
-                        if (a0 + 1 < A.na) d1 = __ldg(A.D + (int64_t)A.nt * (a0 + 1) + row) * sc;
-                    }
-                    split_f16x2(d0, d1, rh[j], rl[j]);
-                }
-                tmem_st8(ta + (uint32_t)c0, rh);
-                tmem_st8(ta + (uint32_t)(half + c0), rl);
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&d_ready);
-        }
         for (int r = 0; !stop; ++r) {
             const int brick = live_brick(A, G, cta, r);
             if (brick < 0) break;
@@ -1597,37 +1603,70 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 }
                 tc_fence_after();
                 if constexpr (F32) {
-                    // Y[θ, tile row]: this thread holds θ = row; 32 tile rows per load, their
-                    // voxels shuffled from the lanes that read them
+                    // Y[θ, tile row]: each 32 x 32 block (this warp's θ quarter, 32 tile
+                    // rows) goes through the warp's shared-memory tile, transposed, so that
+                    // lane i then owns tile row 32·g4 + i and reads b / writes y for its 32
+                    // θ values with 16-byte accesses.  The accumulator is handed back to the
+                    // MMA thread as soon as its last block is in registers.
+                    float* Tw = Ts + q * (32 * DSC_TW);
                     const uint32_t taddr = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)A.kp;
-                    const bool th_ok = row < A.nt;
+                    const int th0 = 32 * q, nth = min(32, A.nt - th0);  // θ of this warp
+                    const bool vec = A.vec4 != 0;
                     float sqf = 0.0f;
                     uint32_t am = 0u;  // bits of max |y| over this warp's θ and the tile's rows
+                    bool released = false;
 #pragma unroll
                     for (int g4 = 0; g4 < 4; ++g4) {
+                        if (nth <= 0) break;  // a θ quarter beyond Nθ (warp-uniform)
+                        const int v = vj[g4];
+                        const int64_t o = (int64_t)A.nt * (v >= 0 ? v : 0) + th0;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            // 16 tile rows: their b values are loaded together, then combined
+                        for (int h2 = 0; h2 < 2; ++h2) {  // 16 tile rows per load
                             uint32_t rr[16];
-                            float bv[16];
-                            tmem_ld16(taddr + (uint32_t)(32 * g4 + 16 * h), rr);
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int v = __shfl_sync(0xffffffffu, vj[g4], 16 * h + e);
-                                bv[e] = (A.b && v >= 0 && th_ok) ? __ldg(A.b + (int64_t)A.nt * v + row) : 0.0f;
-                            }
+                            tmem_ld16(taddr + (uint32_t)(32 * g4 + 16 * h2), rr);
                             tmem_ld_wait();
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int v = __shfl_sync(0xffffffffu, vj[g4], 16 * h + e);
-                                if (v >= 0 && th_ok) {
-                                    const float y = __uint_as_float(rr[e]) * y_unscale - bv[e];
-                                    if (wy) A.out[(int64_t)A.nt * v + row] = y;
+                            for (int e = 0; e < 16; ++e) Tw[(16 * h2 + e) * DSC_TW + lane] = __uint_as_float(rr[e]);
+                        }
+                        if (g4 == 3) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+                            released = true;
+                        }
+                        __syncwarp();
+                        if (v >= 0) {
+                            const float* trow = Tw + lane * DSC_TW;
+                            if (vec) {
+                                // the row's b values, all loads issued before their first use
+                                float4 bv[8];
+#pragma unroll
+                                for (int m = 0; m < 8; ++m)
+                                    bv[m] = (A.b && 4 * m < nth) ? __ldg(reinterpret_cast<const float4*>(A.b + o) + m)
+                                                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                                for (int m = 0; m < 8; ++m) {
+                                    if (4 * m >= nth) break;
+                                    float4 yv = make_float4(trow[4 * m] * y_unscale - bv[m].x,
+                                                            trow[4 * m + 1] * y_unscale - bv[m].y,
+                                                            trow[4 * m + 2] * y_unscale - bv[m].z,
+                                                            trow[4 * m + 3] * y_unscale - bv[m].w);
+                                    if (wy) reinterpret_cast<float4*>(A.out + o)[m] = yv;
+                                    sqf += yv.x * yv.x + yv.y * yv.y + yv.z * yv.z + yv.w * yv.w;
+                                    am = max(max(am, max(abs_bits(yv.x), abs_bits(yv.y))),
+                                             max(abs_bits(yv.z), abs_bits(yv.w)));
+                                }
+                            } else {
+                                for (int k = 0; k < nth; ++k) {
+                                    float y = trow[k] * y_unscale;
+                                    if (A.b) y -= __ldg(A.b + o + k);
+                                    if (wy) A.out[o + k] = y;
                                     sqf += y * y;
                                     am = max(am, abs_bits(y));
                                 }
                             }
                         }
+                        __syncwarp();  // the tile is rewritten by the next block
                     }
                     sq += (double)sqf;
                     if (wy) {
@@ -1636,9 +1675,11 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                         am = warp_max_u32(am);
                         if (lane == 0) A.tile_amax[(int64_t)t * 4 + q] = am;
                     }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[ab]);
+                    if (!released) {  // a warp with no θ of its own
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acc_empty[ab]);
+                    }
                     ++tcount;
                     continue;
                 }
@@ -1719,7 +1760,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
             bulk_copy_g2s(Ss + z * STG, g_zero_chunk, DS_BYTES, &zero_bar[z]);
             bulk_copy_g2s(Ss + z * STG + DS_BYTES, g_zero_chunk, DS_BYTES, &zero_bar[z]);
         }
-        // D's parts are in tensor memory once the four epilogue warps have stored theirs
+        // D's parts are in tensor memory once every producer and epilogue warp has stored its share
         if (!mbar_wait(&d_ready, 0, &abort_flag, WAIT_LIMIT)) {
             abort_flag = 1;
             stop = true;

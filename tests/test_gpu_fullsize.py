@@ -92,15 +92,27 @@ def test_paper_scale_bf16_tc(life, paper):
     idx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_paper_scale_fp32_tc(life, paper):
+    """FP32 storage on the tensor cores (split FP16 operands) at the FP32 tolerance."""
+    p = paper
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    idx = life.upload_problem(p, precision=life.LIFE_FP32, algo=life.LIFE_ALGO_TC)
+    info = idx.info()
+    assert info["algo"] == life.LIFE_ALGO_TC and info["precision"] == life.LIFE_FP32
+    print("paper fp32-tc", sampled_check(life, p, idx, D32, TOL_FP32, bf16=False))
+    idx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32-tc", "bf16"])
 def test_medium_full_and_sbb_step(life, precision):
     p = synth.config_problem("medium")
     D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
     phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
     b = oracle.problem_signal(phi, D32, p.w_true, p.noise, p.n_theta, p.n_voxels)
     bf = precision == "bf16"
+    tc = precision != "fp32"
     idx = life.upload_problem(p, precision=life.LIFE_BF16 if bf else life.LIFE_FP32,
-                              algo=life.LIFE_ALGO_TC if bf else life.LIFE_ALGO_SIMT)
+                              algo=life.LIFE_ALGO_TC if tc else life.LIFE_ALGO_SIMT)
     tol = TOL_BF16 if bf else TOL_FP32
     D = torch.from_numpy(D32).cuda()
     y, _ = life.life_dsc(idx, D, torch.from_numpy(p.w_true).cuda())
@@ -118,8 +130,10 @@ def test_medium_full_and_sbb_step(life, precision):
     w_ref = np.ones(p.n_fasc)
     ost = oracle.sbb_step(phi, D32, b, w_ref, p.n_theta, p.n_voxels, p.n_fasc, oracle.SbbState())
     gst = life.read_sbb_state(st)
-    stol = 1e-4 if not bf else 3e-2
+    # FP32 on the tensor cores: the step's dot products carry its DSC error (a few
+    # 1e-6 of |Mw|) amplified by |Mw| / |e| and the cancellation in M^T e
+    stol = 3e-2 if bf else (1e-3 if tc else 1e-4)
     for k in ("obj", "gg", "vv", "alpha"):
         assert abs(gst[k] - getattr(ost, k)) <= stol * abs(getattr(ost, k)), (k, gst[k], getattr(ost, k))
-    assert rel(w.cpu().numpy(), w_ref) <= (1e-4 if not bf else 3e-2)
+    assert rel(w.cpu().numpy(), w_ref) <= (3e-2 if bf else 1e-4)
     print(precision, "medium", ey, eg)
