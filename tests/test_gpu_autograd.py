@@ -72,12 +72,17 @@ def gpu_loss_and_grads(life, idx, p, w, r, lam_value):
     e = y.double() - torch.from_numpy(r).cuda().double()
     L = 0.5 * (e * e).sum()
     L.backward()
-    return float(L), wt.grad.cpu().numpy(), D.grad.cpu().numpy(), float(lam.grad)
+    return float(L.detach()), wt.grad.cpu().numpy(), D.grad.cpu().numpy(), float(lam.grad)
 
 
-def test_gradients_vs_oracle_fp32(life, case):
+@pytest.mark.parametrize("algo", ["simt", "tc"])
+def test_gradients_vs_oracle_fp32(life, case, algo):
+    """FP32 storage, forward and WC backward on the CUDA cores or on the tensor
+    cores (split FP16 operands); the same FP32 tolerance."""
     p, phi, w, r, dD64, (L_ref, gw_ref, gD_ref, glam_ref) = case
-    idx = life.upload_problem(p, precision=life.LIFE_FP32, algo=life.LIFE_ALGO_SIMT)
+    idx = life.upload_problem(p, precision=life.LIFE_FP32,
+                              algo=life.LIFE_ALGO_SIMT if algo == "simt" else life.LIFE_ALGO_TC)
+    assert idx.info()["algo"] == (life.LIFE_ALGO_SIMT if algo == "simt" else life.LIFE_ALGO_TC)
     tol = 1e-5
     L, gw, gD, glam = gpu_loss_and_grads(life, idx, p, w, r, p.lam)
     torch.cuda.synchronize()

@@ -24,14 +24,17 @@ def life():
     return L
 
 
-def test_bf16_then_fp32_single(life):
+@pytest.mark.parametrize("hi_algo", ["simt", "tc"])
+def test_bf16_then_fp32_single(life, hi_algo):
+    """The FP32 phase on the CUDA cores or on the tensor cores (split FP16 operands)."""
     p = synth.config_problem("tiny")
     D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
     phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
     b = torch.from_numpy(oracle.problem_signal(phi, D32, p.w_true, p.noise, p.n_theta, p.n_voxels)).cuda()
     D = torch.from_numpy(D32).cuda()
     lo = life.upload_problem(p, precision=life.LIFE_BF16, algo=life.LIFE_ALGO_TC)
-    hi = life.upload_problem(p, precision=life.LIFE_FP32, algo=life.LIFE_ALGO_SIMT)
+    hi = life.upload_problem(p, precision=life.LIFE_FP32,
+                             algo=life.LIFE_ALGO_SIMT if hi_algo == "simt" else life.LIFE_ALGO_TC)
     tol = 1e-4
     # FP32 alone
     w_ref = torch.ones(p.n_fasc, device="cuda")

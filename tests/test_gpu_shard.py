@@ -42,7 +42,7 @@ def case():
     return p, D32, phi, b
 
 
-PATHS = {"fp32": (0, 1, 1e-5), "bf16": (1, 2, 3e-3)}   # precision, algo, tolerance
+PATHS = {"fp32": (0, 1, 1e-5), "fp32-tc": (0, 2, 1e-5), "bf16": (1, 2, 3e-3)}   # precision, algo, tolerance
 
 
 def shard_indices(life, p, ranges, precision, algo):
@@ -54,7 +54,7 @@ def shard_indices(life, p, ranges, precision, algo):
                                         voxel_ijk=ijk, precision=precision, algo=algo) for v0, v1 in ranges]
 
 
-@pytest.mark.parametrize("path", ["fp32", "bf16"])
+@pytest.mark.parametrize("path", ["fp32", "fp32-tc", "bf16"])
 def test_shard_spmv(life, case, path):
     p, D32, phi, b = case
     prec, algo, tol = PATHS[path]
@@ -76,7 +76,7 @@ def test_shard_spmv(life, case, path):
     assert rel(g, oracle.wc(phi, D32, r, nt, nf)) <= tol
 
 
-@pytest.mark.parametrize("path,n_shards", [("fp32", 2), ("fp32", 3), ("bf16", 2)])
+@pytest.mark.parametrize("path,n_shards", [("fp32", 2), ("fp32", 3), ("fp32-tc", 2), ("bf16", 2)])
 def test_sharded_sbb_teacher_forced(life, case, path, n_shards):
     p, D32, phi, b = case
     prec, algo, _ = PATHS[path]
@@ -91,7 +91,7 @@ def test_sharded_sbb_teacher_forced(life, case, path, n_shards):
     # BF16: six iterations, as for the unsharded tensor-core path; later ones cancel
     # the projected gradient so strongly that BF16 storage alone moves <g~,g~> by
     # several per cent
-    for it in range(10 if path == "fp32" else 6):
+    for it in range(6 if path == "bf16" else 10):
         w_in = shards[0].w.double().cpu().numpy().copy()
         prev = life.read_sbb_state(shards[0].st)
         ost.s.it, ost.s.alpha, ost.s.gg0 = prev["it"], prev["alpha"], prev["gg0"]
@@ -110,6 +110,12 @@ def test_sharded_sbb_teacher_forced(life, case, path, n_shards):
         worst["w"] = max(worst.get("w", 0.0), rel(ws[0], w_in))
     life.life_check_device_status()
     print(path, n_shards, worst)
+    if path == "fp32-tc":
+        # as unsharded: the step's dot products carry the tensor-core DSC error
+        # (~3e-6 of |Mw|) amplified near the fit; the objective and w stay at 1e-4
+        assert worst["obj"] <= 1e-4 and worst["w"] <= 1e-4, worst
+        assert max(worst.values()) <= 1e-2, worst
+        return
     lim = 1e-4 if path == "fp32" else 3e-2
     assert max(worst.values()) <= lim, worst
 

@@ -385,3 +385,16 @@ def test_tc32_batch(life):
         assert sb[k]["converged"] == ss["converged"] == 1
         assert abs(sb[k]["obj"] - ss["obj"]) <= 1e-3 * ss["obj"]
         assert rel(wb[k].cpu().numpy(), w.cpu().numpy()) <= 1e-2
+
+
+def test_tc32_autotune(life):
+    """The autotuner on an FP32 tensor-core index: it times brick edges and WC
+    scatter groups as for BF16 storage, and the chosen layout keeps the FP32
+    tolerance."""
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    idx = life.upload_problem(p, precision=life.LIFE_FP32, algo=life.LIFE_ALGO_TC, autotune=True)
+    info = idx.info()
+    assert info["tuned"] == 1 and info["algo"] == life.LIFE_ALGO_TC and info["wc_groups"] in (1, 2, 4)
+    run_check(life, idx, phi, D32, p.n_theta, p.n_atoms, p.n_voxels, p.n_fasc, seed=9)
