@@ -153,14 +153,15 @@ struct TileLayout {
     int vbytes = 2;          // bytes per stored value: 2 for BF16 storage, 4 for FP32 storage
     bool wc_stream = true;   // the WC streams and their per-brick bounds exist (BF16 storage: the
                              // FP32-storage index runs WC on the CUDA cores)
-    // DSC brick weight tables: brick b's weights w[brick_fasc[...]] are gathered,
-    // before each DSC launch, into wb[wb_ptr[b] ..) (16-byte aligned, padded to a
-    // multiple of 4 floats) so a CTA loads a brick's table with one bulk copy
+    // DSC brick weight tables: brick b's slots are wb_ptr[b] .. (padded to a multiple
+    // of 4); the DSC gathers w[wb_src[slot]] into shared memory at each brick start,
+    // or, on the live-entry stream, a kernel gathers them into wb before the launch
+    // and a CTA loads a brick's table with one bulk copy
     int64_t wb_total = 0;
     int64_t n_brick_slots = 0;  // real (unpadded) slots of the brick weight tables
-    DevBuf wb_src;           // int32 [wb_total]: global fascicle of each slot (0 for padding)
+    DevBuf wb_src;           // int32 [wb_total]: global fascicle of each slot (-1 for padding)
     DevBuf wb_ptr;           // int32 [n_bricks + 1], multiples of 4
-    DevBuf wb;               // float [wb_total]: gathered weights (rewritten by every DSC call)
+    DevBuf wb;               // float [wb_total]: gathered weights (live-entry stream only)
     // WC fixed-point tables: per brick, an upper bound on Σ|val| over the entries of
     // any one brick-local fascicle; per tile, the bits of max |r| over its voxels
     // Live-entry DSC stream (sparse-w-aware DSC): the DSC stream restricted to the

@@ -125,25 +125,16 @@ __device__ __forceinline__ void block_absmax_out(uint32_t m, uint32_t* out) {
     }
 }
 
-// wb[j] = w[wb_src[j]] (0 for padding slots): the DSC's brick weight tables for
-// this call's w, and per block the bits of max |w| over the gathered slots (the
-// scale of the DSC's FP16 S operand).  (n is a multiple of 4 and both arrays are
-// 16-byte aligned: each thread moves 4 slots per step with one 16-byte load of
-// indices, four independent gathers and one 16-byte store.)  The launch (8 blocks
-// of 256 threads per SM) is one full wave only at <= 32 registers per thread.
-__global__ void __launch_bounds__(256, 8) wb_gather_kernel(const int32_t* __restrict__ wsrc, int64_t n, const float* __restrict__ w,
-                                 float* __restrict__ wb, uint32_t* __restrict__ amax) {
-    const int64_t n4 = n >> 2;
+// Per block, the bits of max |x| over the finite values of x: the scale of the
+// DSC's FP16 S operand when the DSC gathers each brick's weights itself.  (A NaN
+// or inf weight makes its run sums non-finite whatever the scale; leaving it out
+// keeps every other S value scaled into FP16's range.)  One block per SM.
+__global__ void __launch_bounds__(256) x_amax_kernel(const float* __restrict__ x, int64_t n,
+                                                     uint32_t* __restrict__ amax) {
     uint32_t m = 0u;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
-        const int4 id = __ldg(reinterpret_cast<const int4*>(wsrc) + j);
-        float4 v;
-        v.x = gather_slot(w, id.x);
-        v.y = gather_slot(w, id.y);
-        v.z = gather_slot(w, id.z);
-        v.w = gather_slot(w, id.w);
-        reinterpret_cast<float4*>(wb)[j] = v;
-        m = max(m, absmax4_bits(v));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t bits = __float_as_uint(__ldg(x + i)) & 0x7FFFFFFFu;
+        if (bits < 0x7F800000u) m = max(m, bits);
     }
     block_absmax_out(m, amax);
 }
@@ -752,7 +743,12 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         L.n_brick_slots = hbptr[H.n_bricks];
         LIFE_TRY(upload(L.wb_ptr, wptr, s));
         LIFE_TRY(L.wb_src.alloc(sizeof(int32_t) * std::max<int64_t>(L.wb_total, 4)));
-        LIFE_TRY(L.wb.alloc(sizeof(float) * std::max<int64_t>(L.wb_total, 4)));
+        // gathered tables in global memory serve only the live-entry stream (the
+        // dense DSC gathers each brick's weights itself)
+        if (ix->sparse_dsc != 0 && ix->batch.vox_group.empty())
+            LIFE_TRY(L.wb.alloc(sizeof(float) * std::max<int64_t>(L.wb_total, 4)));
+        else
+            L.wb.release();
         if (H.n_bricks > 0) {
             wb_src_kernel<<<(unsigned)std::min<int64_t>(H.n_bricks, 65535), 128, 0, s>>>(
                 L.brick_fasc_ptr.as<int32_t>(), L.brick_fasc.as<int32_t>(), L.wb_ptr.as<int32_t>(),
@@ -970,7 +966,9 @@ struct TcArgs {
     double* partial;     // DSC: per-CTA FP64 Σ out²
     const float* val32;  // DSC on an FP32-storage index: the stream's values (val is then unused)
     const float* wval32; // WC on an FP32-storage index: the WC stream's values (wval is then unused)
-    const float* wb;     // DSC: gathered brick weight tables
+    const float* wb;     // DSC on the live-entry stream: brick weight tables gathered before the launch
+    const int32_t* wb_src;  // DSC: global fascicle of each brick-table slot (-1 for padding)
+    int gather_w;        // DSC: 1 = the producers gather each brick's table from x themselves
     const int32_t* wb_ptr;
     const float* brick_cv;    // WC: per-brick bound on Σ|val| of one fascicle
     uint32_t* tile_amax;      // bits of |r| maxima, 4 slots per tile (their max is the tile's): DSC writes, WC reads
@@ -1486,17 +1484,46 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                         abort_flag = 1;
                         break;
                     }
-                    if (tid == 0) {  // one bulk copy of the brick's gathered weights
+                    if (A.gather_w) {
+                        // the brick's weights straight from x: slot i holds x[wb_src[o + i]]
+                        // (0 for padding); GW slots a round, loads first
+                        constexpr int GW = 8;
                         const int o = A.wb_ptr[brick], nb4 = A.wb_ptr[brick + 1] - o;
-                        mbar_arrive_expect_tx(&tab_bar, 4u * (uint32_t)nb4);
-                        if (nb4 > 0) bulk_copy_g2s(wl, A.wb + o, 4u * (uint32_t)nb4, &tab_bar);
+                        for (int i0 = tid; i0 < nb4; i0 += GW * DSC_PROD_THREADS) {
+                            int32_t id[GW];
+#pragma unroll
+                            for (int k = 0; k < GW; ++k) {
+                                const int i = i0 + k * DSC_PROD_THREADS;
+                                id[k] = i < nb4 ? __ldg(A.wb_src + o + i) : -1;
+                            }
+                            float xv[GW];
+#pragma unroll
+                            for (int k = 0; k < GW; ++k) xv[k] = id[k] >= 0 ? __ldg(A.x + id[k]) : 0.0f;
+#pragma unroll
+                            for (int k = 0; k < GW; ++k)
+                                if (i0 + k * DSC_PROD_THREADS < nb4) wl[i0 + k * DSC_PROD_THREADS] = xv[k];
+                        }
+                        // the next brick's slot indices into L2 (they come from DRAM)
+                        int rn = r + 1;
+                        const int nbk = live_brick(A, G, cta, rn);
+                        if (nbk >= 0) {
+                            const int o2 = A.wb_ptr[nbk], n2 = A.wb_ptr[nbk + 1] - o2;
+                            for (int i = 32 * tid; i < n2; i += 32 * DSC_PROD_THREADS) prefetch_l2(A.wb_src + o2 + i);
+                        }
+                        named_bar_sync(1, DSC_PROD_THREADS);  // the table is complete
+                    } else {
+                        if (tid == 0) {  // one bulk copy of the brick's gathered weights
+                            const int o = A.wb_ptr[brick], nb4 = A.wb_ptr[brick + 1] - o;
+                            mbar_arrive_expect_tx(&tab_bar, 4u * (uint32_t)nb4);
+                            if (nb4 > 0) bulk_copy_g2s(wl, A.wb + o, 4u * (uint32_t)nb4, &tab_bar);
+                        }
+                        if (!warp_wait(&tab_bar, tab_ph, &abort_flag)) {
+                            abort_flag = 1;
+                            dead = true;
+                        }
+                        tab_ph ^= 1u;
+                        ++tab_n;
                     }
-                    if (!warp_wait(&tab_bar, tab_ph, &abort_flag)) {
-                        abort_flag = 1;
-                        dead = true;
-                    }
-                    tab_ph ^= 1u;
-                    ++tab_n;
                 }
                 const uint32_t st = cc % DSTAGE, ph = (cc / DSTAGE) & 1u;
                 unsigned char* S = Ss + st * STG;
@@ -2787,10 +2814,12 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
                 !gate ? ALLOW_FREE : (gate_mode == GATE_ACTIVE ? ALLOW_NONE : ALLOW_BACKOFF), gate, gate_mode,
                 L.x_amax.as<uint32_t>());
         else
-            wb_gather_kernel<<<ix->num_sms * 8, GATHER_THREADS, 0, s>>>(L.wb_src.as<int32_t>(), L.wb_total, w,
-                                                                      L.wb.as<float>(), L.x_amax.as<uint32_t>());
+            // the DSC gathers each brick's weights itself; this pass only finds max |w|
+            x_amax_kernel<<<ix->num_sms, 256, 0, s>>>(w, ix->nf, L.x_amax.as<uint32_t>());
         A.x_amax = L.x_amax.as<uint32_t>();
-        A.n_xamax = ix->num_sms * 8;
+        A.n_xamax = sparse ? ix->num_sms * 8 : ix->num_sms;
+        A.gather_w = sparse ? 0 : 1;
+        A.wb_src = L.wb_src.as<int32_t>();
         LIFE_CHECK_LAUNCH();
     }
     auto kern = f32 ? dsc_tc_kernel<true> : dsc_tc_kernel<false>;
