@@ -31,26 +31,29 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
 # DRAM bytes (read + write) of the launches of one timed tensor-core call, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric
-# set) on the paper-density workload at a third of the size: DSC with the fused
-# residual = brick weight gather + DSC kernel; WC through the public call =
-# per-tile max|r| pass + WC kernel.  Scaled to the timed workload by its entry
-# count (the traffic grows with the entries and voxels alike).  The figures hold
-# only for the kernel source that was captured; after any change to it the bench
-# reports null.
+# ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, one kernel per
+# capture) on the paper-density workload at a third of the size: DSC with the
+# fused residual = max|w| pass + DSC kernel; WC through the public call =
+# per-tile max|r| pass + WC kernel; per path (BF16 storage, FP32 storage on the
+# tensor cores).  Scaled to the timed workload by its entry count (the traffic
+# grows with the entries and voxels alike).  The figures hold only for the kernel
+# source that was captured; after any change to it the bench reports null.
 TRAFFIC_CAPTURE = {
     "src": os.path.join("paper_1905_06234_gb300", "csrc", "spmv_tc.cu"),
-    "sha256": "73b2dd1b6a4306f83f21a97f229b72e2abc6a2fead9865573b9126d62959f318",
+    "sha256": "5980ee3c4bdf0304d89da05dd68d1606e5c1fc8b941f8df2bc6d2d50c66415c2",
     "nnz": 23816750,
-    "bytes": {"dsc": (11041792 + 0) + (193712640 + 16351232),
-              "wc": (39992832 + 0) + (202023936 + 66816)},
+    "bytes": {
+        "bf16-tc": {"dsc": (607488 + 0) + (197685504 + 16750848), "wc": (39997440 + 0) + (202008832 + 57344)},
+        "fp32-tc": {"dsc": (607232 + 0) + (248770304 + 20284416), "wc": (39995392 + 0) + (252619520 + 139008)},
+    },
 }
 
 
 def kernel_traffic(path_name, kind, nnz):
     """Measured DRAM bytes of one launch (scaled to `nnz` entries if the workload differs), or None."""
     import hashlib
-    if not path_name.startswith("bf16-tc"):
+    per_path = TRAFFIC_CAPTURE["bytes"].get(path_name)
+    if per_path is None:
         return None
     try:
         with open(os.path.join(ROOT, TRAFFIC_CAPTURE["src"]), "rb") as fh:
@@ -59,7 +62,7 @@ def kernel_traffic(path_name, kind, nnz):
         return None
     if sha != TRAFFIC_CAPTURE["sha256"]:
         return None
-    return TRAFFIC_CAPTURE["bytes"][kind] * nnz / TRAFFIC_CAPTURE["nnz"]
+    return per_path[kind] * nnz / TRAFFIC_CAPTURE["nnz"]
 
 
 def read_peaks():
@@ -708,6 +711,8 @@ def run_ours(args):
                       "dsc_frac": v["kern"]["dsc_bytes"] / v["kern"]["dsc_s"] / 1e9 / peak,
                       "wc_frac": v["kern"]["wc_bytes"] / v["kern"]["wc_s"] / 1e9 / peak,
                       "vs_fp32_simt": results["fp32-simt"]["dt"] / v["dt"],
+                      "dsc_traffic": kernel_traffic(k, "dsc", v["path"].info["nnz"]),
+                      "wc_traffic": kernel_traffic(k, "wc", v["path"].info["nnz"]),
                       "index_build_s": v["path"].build_s} for k, v in results.items()},
         "vs_plain_fp32": (args.steps / best["dt"]) / (args.steps / results["fp32-simt"]["dt"]),
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
