@@ -26,6 +26,7 @@ namespace life {
 using namespace ptx;
 
 constexpr int SUB = 32;                  // atoms per sub-chunk (offset granularity)
+constexpr int ZW = 33;                   // row stride (floats) of a WC scatter warp's 32 x 32 Z tile
 constexpr uint16_t CONT = 0x8000;        // entry continues the previous entry's (atom, row)
 constexpr uint64_t WAIT_LIMIT = 2000000000ull; // ns before a wait gives up
 
@@ -392,7 +393,7 @@ __global__ void brick_cv_kernel(const int32_t* __restrict__ btile, const int32_t
         const int32_t j0 = wseg_ptr[(int64_t)btile[b] * seg_per_tile], j1 = wseg_ptr[(int64_t)btile[b + 1] * seg_per_tile];
         uint32_t vm = 0u;
         for (int32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            atomicAdd(&cnt[wfl[j]], 1);
+            atomicAdd(&cnt[wfl[j] >> 2], 1);
             vm = max(vm, __float_as_uint(__bfloat162float(wval[j])) & 0x7FFFFFFFu);
         }
         for (int o = 16; o > 0; o >>= 1) vm = max(vm, __shfl_xor_sync(0xffffffffu, vm, o));
@@ -470,15 +471,19 @@ __global__ void wc_key_kernel(const uint64_t* __restrict__ skey, int64_t m, int 
 template <class VT>
 __global__ void wc_stream_kernel(const uint64_t* __restrict__ key3, const uint32_t* __restrict__ pay3, int64_t m,
                                  int bf, const uint16_t* __restrict__ fl, const VT* __restrict__ val,
-                                 int32_t n_sub, int64_t n_segs, uint16_t* __restrict__ wkey, uint16_t* __restrict__ wfl,
-                                 VT* __restrict__ wval, int32_t* __restrict__ wseg_ptr) {
+                                 int32_t n_sub, int64_t n_segs, int atom_major, uint16_t* __restrict__ wkey,
+                                 uint16_t* __restrict__ wfl, VT* __restrict__ wval, int32_t* __restrict__ wseg_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = key3[j];
         const uint32_t src = pay3[j];
         const uint64_t t = k >> (16 + bf), q = (k >> (14 + bf)) & 3u, a = (k >> (5 + bf)) & 511u,
                        r32 = (k >> bf) & 31u;
-        wkey[j] = (uint16_t)(r32 | ((a & 31u) << 5));
-        wfl[j] = (uint16_t)(fl[src] & 0x7FFFu);
+        // byte offsets: of the entry's (row, atom) cell in a scatter warp's Z tile
+        // (row-major, or atom-major for the FP32-storage kernel) and of its
+        // fascicle in the brick table (< 15872 fascicles: fits 16 bits)
+        const uint32_t cell = atom_major ? (uint32_t)(a & 31u) * ZW + (uint32_t)r32 : (uint32_t)r32 * ZW + (uint32_t)(a & 31u);
+        wkey[j] = (uint16_t)(4u * cell);
+        wfl[j] = (uint16_t)(4u * (fl[src] & 0x7FFFu));
         wval[j] = val[src];
         const int64_t seg = ((int64_t)t * 4 + (int64_t)q) * n_sub + (int64_t)(a >> 5);
         int64_t segp = -1;
@@ -831,13 +836,13 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
             LIFE_TRY(radix_sort_pairs(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, nbits64(H.n_tiles) + 16 + bf, s));
             if (L.vbytes == 4)
                 wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
-                                                           L.fl.as<uint16_t>(), L.val.as<float>(), L.n_sub, n_wsegs,
+                                                           L.fl.as<uint16_t>(), L.val.as<float>(), L.n_sub, n_wsegs, 1,
                                                            L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
                                                            L.wval.as<float>(), L.wseg_ptr.as<int32_t>());
             else
                 wc_stream_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
                                                            L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), L.n_sub,
-                                                           n_wsegs, L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
+                                                           n_wsegs, 0, L.wkey.as<uint16_t>(), L.wfl.as<uint16_t>(),
                                                            L.wval.as<__nv_bfloat16>(), L.wseg_ptr.as<int32_t>());
             LIFE_CHECK_LAUNCH();
         } else {
@@ -1915,7 +1920,6 @@ constexpr int WC_MMA_WARP = WC_SCAT_WARPS + WC_LOAD_WARPS;
 constexpr int WC_THREADS = (WC_MMA_WARP + 1) * 32;
 constexpr int WC_SCAT_THREADS = WC_SCAT_WARPS * 32;
 constexpr int WC_LOAD_THREADS = WC_LOAD_WARPS * 32;
-constexpr int ZW = 33;                                // row stride (floats) of a warp's Z tile
 // Z goes through tensor memory in 128-atom chunks: a ring of ZSLOTS slots of 128
 // columns (all 512), so the tensor cores can fill the next chunks while the
 // scatter warps still work on earlier ones
@@ -1935,29 +1939,31 @@ __host__ __device__ inline uint32_t wc_smem_bytes(int np, int kp, int max_fb, in
 }
 
 // FIXED: the table holds 32-bit integers in units of 1/sc' (sc' a power of two chosen
-// so that no partial sum can leave the int32 range); otherwise FP32.  sc carries
-// also the removal of the operand scales from Z: x = val·Z·sc is in table units.
+// so that no partial sum can leave the int32 range); otherwise FP32.  The Z tile
+// holds Z·sc, sc also removing the operand scales from Z, so x = val·Z·sc is in
+// table units.  The stream's key and fascicle are byte offsets into the Z tile and
+// the table.
 template <bool CHECK, bool FIXED>
 __device__ __forceinline__ void wc_slot_t(const EntrySlot& s, int base, int beg, int end, const float* Zw,
-                                          float* gl, uint32_t gl_s, float sc) {
+                                          float* gl, uint32_t gl_s) {
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
         if (CHECK) {
             const int idx = base + e;
             if (idx < beg || idx >= end) continue;
         }
-        const uint32_t k = u16_at(s.key, e);
-        const float x = bf16_at(s.val, e) * Zw[(k & 31u) * ZW + (k >> 5)] * sc;
-        if (FIXED) atomicAdd(reinterpret_cast<int*>(gl) + u16_at(s.fl, e), __float2int_rn(x));
-        else red_add_shared_f32(gl_s + 4u * u16_at(s.fl, e), x);
+        const float z = *reinterpret_cast<const float*>(reinterpret_cast<const char*>(Zw) + u16_at(s.key, e));
+        const float x = bf16_at(s.val, e) * z;
+        if (FIXED) atomicAdd(reinterpret_cast<int*>(reinterpret_cast<char*>(gl) + u16_at(s.fl, e)), __float2int_rn(x));
+        else red_add_shared_f32(gl_s + u16_at(s.fl, e), x);
     }
 }
 
 template <bool FIXED>
 __device__ __forceinline__ void wc_slot(const EntrySlot& s, int base, int beg, int end, const float* Zw, float* gl,
-                                        uint32_t gl_s, float sc) {
-    if (base >= beg && base + SLOT <= end) wc_slot_t<false, FIXED>(s, base, beg, end, Zw, gl, gl_s, sc);
-    else wc_slot_t<true, FIXED>(s, base, beg, end, Zw, gl, gl_s, sc);
+                                        uint32_t gl_s) {
+    if (base >= beg && base + SLOT <= end) wc_slot_t<false, FIXED>(s, base, beg, end, Zw, gl, gl_s);
+    else wc_slot_t<true, FIXED>(s, base, beg, end, Zw, gl, gl_s);
 }
 
 __device__ __forceinline__ void wc_load_slot(const TcArgs& A, int base, EntrySlot& s) {
@@ -2117,7 +2123,8 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
             const float bnd = A.brick_cv[brick] * __uint_as_float(d1_bits) * __uint_as_float(am);
             int bexp = 0;
             (void)frexpf(bnd, &bexp);
-            const bool fixed = bnd <= 3.0e38f && bnd >= 1.0e-27f;
+            // (Z·sc < 2^29 / cv must also stay finite: cv >= 1e-28)
+            const bool fixed = bnd <= 3.0e38f && bnd >= 1.0e-27f && A.brick_cv[brick] >= 1.0e-28f;
             // Z in tensor memory carries the operand scales 2^(kR + kD); the table
             // unit 2^(bexp - 29) is in true units (sc folds both in, exactly)
             const int kZ = f16_scale_exp(am) + kD;
@@ -2173,7 +2180,7 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                                 tmem_ld_wait();
                                 float* zrow = Zw + lane * ZW;
 #pragma unroll
-                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]) * sc;
                                 __syncwarp();
                                 for (;;) {
                                     const int b2 = base + 2 * BLK;
@@ -2186,11 +2193,11 @@ __global__ void __maxnreg__(96) wc_tc_kernel(TcArgs A) {
                                         if (nbase + BLK < nend) wc_load_slot(A, nbase + BLK, nxt1);
                                     }
                                     if (fixed) {
-                                        wc_slot<true>(cur0, base, beg, end, Zw, gl, gl_s, sc);
-                                        wc_slot<true>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                        wc_slot<true>(cur0, base, beg, end, Zw, gl, gl_s);
+                                        wc_slot<true>(cur1, base + BLK, beg, end, Zw, gl, gl_s);
                                     } else {
-                                        wc_slot<false>(cur0, base, beg, end, Zw, gl, gl_s, sc);
-                                        wc_slot<false>(cur1, base + BLK, beg, end, Zw, gl, gl_s, sc);
+                                        wc_slot<false>(cur0, base, beg, end, Zw, gl, gl_s);
+                                        wc_slot<false>(cur1, base + BLK, beg, end, Zw, gl, gl_s);
                                     }
                                     if (!more) break;
                                     cur0 = nxt0;
@@ -2384,16 +2391,16 @@ constexpr int Z32_SLOTS = 3;
 
 template <bool CHECK>
 __device__ __forceinline__ void wc32_slot_t(const EntrySlot32& s, int base, int beg, int end, const float* Zw,
-                                            uint32_t gl_s, float sc) {
+                                            uint32_t gl_s) {
 #pragma unroll
     for (int e = 0; e < SLOT; ++e) {
         if (CHECK) {
             const int idx = base + e;
             if (idx < beg || idx >= end) continue;
         }
-        const uint32_t k = u16_at(s.key, e);  // (row mod 32) | (atom mod 32) << 5
-        const float x = slot_val(s, e) * Zw[(k >> 5) * ZW + (k & 31u)] * sc;
-        red_add_shared_f32(gl_s + 4u * u16_at(s.fl, e), x);
+        // key: byte offset of (atom, row) in the atom-major Z tile, which holds Z·sc
+        const float z = *reinterpret_cast<const float*>(reinterpret_cast<const char*>(Zw) + u16_at(s.key, e));
+        red_add_shared_f32(gl_s + u16_at(s.fl, e), slot_val(s, e) * z);
     }
 }
 
@@ -2406,10 +2413,10 @@ __device__ __forceinline__ void wc32_load_slot(const TcArgs& A, int base, EntryS
 }
 
 // Adds val·Z·sc for the entries [beg, end) of one WC segment (Zw[atom][row] holds
-// the segment's 32 x 32 block of Z); lane i takes entries 8i .. of each
+// the segment's 32 x 32 block of Z·sc); lane i takes entries 8i .. of each
 // 256-entry block, the next block loaded while the current one is processed.
 __device__ __forceinline__ void wc32_segment(const TcArgs& A, int beg, int end, const float* Zw, uint32_t gl_s,
-                                             float sc, int lane) {
+                                             int lane) {
     int base = (beg & ~7) + lane * SLOT;
     EntrySlot32 cur{};
     if (base < end) wc32_load_slot(A, base, cur);
@@ -2418,8 +2425,8 @@ __device__ __forceinline__ void wc32_segment(const TcArgs& A, int beg, int end, 
         const bool more = __shfl_sync(0xffffffffu, nb, 0) < end;  // warp-uniform
         EntrySlot32 nxt{};
         if (more && nb < end) wc32_load_slot(A, nb, nxt);
-        if (base >= beg && base + SLOT <= end) wc32_slot_t<false>(cur, base, beg, end, Zw, gl_s, sc);
-        else wc32_slot_t<true>(cur, base, beg, end, Zw, gl_s, sc);
+        if (base >= beg && base + SLOT <= end) wc32_slot_t<false>(cur, base, beg, end, Zw, gl_s);
+        else wc32_slot_t<true>(cur, base, beg, end, Zw, gl_s);
         if (!more) break;
         cur = nxt;
         base = nb;
@@ -2556,9 +2563,9 @@ __global__ void __maxnreg__(96) wc_tc32_kernel(TcArgs A) {
                                 tmem_ld_wait();
                                 float* zrow = Zw + lane * ZW;  // this lane's atom, the row quarter's 32 rows
 #pragma unroll
-                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]);
+                                for (int e = 0; e < 32; ++e) zrow[e] = __uint_as_float(rr[e]) * sc;
                                 __syncwarp();
-                                wc32_segment(A, beg, end, Zw, gl_s, sc, lane);
+                                wc32_segment(A, beg, end, Zw, gl_s, lane);
                                 __syncwarp();
                             }
                         }
