@@ -142,13 +142,15 @@ struct TileLayout {
     DevBuf brick_fasc;       // int32 [sum] global fascicle id of each brick-local fascicle
     DevBuf brick_order;      // int32 [n_bricks] bricks by decreasing entry count
     DevBuf va;               // uint16 [n_nnz]: row | (atom << 7)
-    DevBuf soff;             // uint16 [n_nnz]: element offset of (row, atom mod 128) in a DSC S chunk
+    DevBuf soff;             // uint16 [n_nnz]: byte offset of (row, atom mod 128) in a DSC S chunk | 0x8000
+                             // if the entry has the same (atom, row) as the previous one
     // WC streams, ordered (tile, row quarter, atom, row, fascicle)
-    DevBuf wkey;             // uint16 [n_nnz]: (row mod 32) | (atom mod 32) << 5
-    DevBuf wfl;              // uint16 [n_nnz]: brick-local fascicle
+    DevBuf wkey;             // uint16 [n_nnz]: byte offset of (row mod 32, atom mod 32) in a scatter
+                             // warp's 32 x 33 Z tile (row-major; atom-major with FP32 storage)
+    DevBuf wfl;              // uint16 [n_nnz]: byte offset of the brick-local fascicle in the table
     DevBuf wval;             // bf16 [n_nnz]
     DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom sub)
-    DevBuf fl;               // uint16 [n_nnz]: brick-local fascicle | 0x8000 if same (atom,row) as previous
+    DevBuf fl;               // uint16 [n_nnz]: byte offset of the brick-local fascicle in the weight table
     DevBuf val;              // [n_nnz] stored values: bf16 (vbytes 2) or float (vbytes 4)
     int vbytes = 2;          // bytes per stored value: 2 for BF16 storage, 4 for FP32 storage
     bool wc_stream = true;   // the WC streams and their per-brick bounds exist (BF16 storage: the

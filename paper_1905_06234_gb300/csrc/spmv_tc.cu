@@ -310,7 +310,9 @@ __device__ __forceinline__ uint32_t slot_live(const uint4& flv, int base, int be
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int j = base + e;
-        if (j >= beg && j < end && wbb[u16_of(flv, e) & 0x7FFFu] != 0.0f) m |= 1u << e;
+        if (j >= beg && j < end &&
+            *reinterpret_cast<const float*>(reinterpret_cast<const char*>(wbb) + u16_of(flv, e)) != 0.0f)
+            m |= 1u << e;
     }
     return m;
 }
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_rebuild_kernel(CompactArgs C)
             }
             const int total = __shfl_sync(0xffffffffu, pre, 31);
             // S offset of this lane's last live entry, and the previous live entry before this lane
-            const uint32_t last_so = m ? u16_of(sov, 31 - __clz(m)) : 0u;
+            const uint32_t last_so = m ? (u16_of(sov, 31 - __clz(m)) & 0x7FFFu) : 0u;
             const uint32_t has = __ballot_sync(0xffffffffu, m != 0u);
             const uint32_t lower = has & below;
             const uint32_t from = __shfl_sync(0xffffffffu, last_so, lower ? 31 - __clz(lower) : lane);
@@ -361,9 +363,9 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_rebuild_kernel(CompactArgs C)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 if (!((m >> e) & 1u)) continue;
-                const uint32_t so = u16_of(sov, e);
-                C.c_soff[q] = (uint16_t)so;
-                C.c_fl[q] = (uint16_t)((u16_of(flv, e) & 0x7FFFu) | (p == so ? CONT : 0u));
+                const uint32_t so = u16_of(sov, e) & 0x7FFFu;
+                C.c_soff[q] = (uint16_t)(so | (p == so ? CONT : 0u));
+                C.c_fl[q] = (uint16_t)u16_of(flv, e);
                 reinterpret_cast<uint16_t*>(C.c_val)[q] = (uint16_t)u16_of(vav, e);
                 p = so;
                 ++q;
@@ -418,7 +420,7 @@ __global__ void local_fasc_kernel(const uint64_t* __restrict__ key2, const uint3
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t b = (int32_t)(key2[j] >> bf);
         const int32_t u = uidx[j] + head[j] - 1;
-        fl[pay2[j]] = (uint16_t)(u - bptr[b]);
+        fl[pay2[j]] = (uint16_t)(4 * (u - bptr[b]));  // byte offset in the brick's weight table
     }
 }
 
@@ -440,9 +442,10 @@ __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint
         const uint64_t t = k >> (16 + bf);
         const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
         va[j] = (uint16_t)(row | (a << 7));
-        soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) >> 1);
+        // byte offset of (row, atom) in an S chunk (< 32768), with the continuation bit
+        const bool cont = j > 0 && (skey[j - 1] >> bf) == (k >> bf);
+        soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) | (cont ? CONT : 0u));
         store_val(val + j, uval[spay[j]]);
-        if (j > 0 && (skey[j - 1] >> bf) == (k >> bf)) fl[j] = (uint16_t)(fl[j] | CONT);
         const int64_t seg = (int64_t)t * n_sub + (a >> 5);
         int64_t segp = -1;
         if (j > 0) {
@@ -483,7 +486,7 @@ __global__ void wc_stream_kernel(const uint64_t* __restrict__ key3, const uint32
         // fascicle in the brick table (< 15872 fascicles: fits 16 bits)
         const uint32_t cell = atom_major ? (uint32_t)(a & 31u) * ZW + (uint32_t)r32 : (uint32_t)r32 * ZW + (uint32_t)(a & 31u);
         wkey[j] = (uint16_t)(4u * cell);
-        wfl[j] = (uint16_t)(4u * (fl[src] & 0x7FFFu));
+        wfl[j] = fl[src];
         wval[j] = val[src];
         const int64_t seg = ((int64_t)t * 4 + (int64_t)q) * n_sub + (int64_t)(a >> 5);
         int64_t segp = -1;
@@ -506,13 +509,13 @@ __global__ void fill_kernel(int32_t* p, int64_t n, int32_t v) {
 // stream (a run starts at an entry without the continuation flag): with max |x|
 // it bounds every S value of a DSC.
 template <class VT>
-__global__ void run_vmax_kernel(const uint16_t* __restrict__ fl, const VT* __restrict__ val, int64_t m,
+__global__ void run_vmax_kernel(const uint16_t* __restrict__ soff, const VT* __restrict__ val, int64_t m,
                                 uint32_t* __restrict__ out) {
     uint32_t best = 0u;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-        if (fl[j] & CONT) continue;
+        if (soff[j] & CONT) continue;
         float sum = fabsf(load_val(val + j));
-        for (int64_t k = j + 1; k < m && (fl[k] & CONT); ++k) sum += fabsf(load_val(val + k));
+        for (int64_t k = j + 1; k < m && (soff[k] & CONT); ++k) sum += fabsf(load_val(val + k));
         best = max(best, __float_as_uint(sum));
     }
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -808,9 +811,9 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         LIFE_TRY(rv.alloc(sizeof(uint32_t), s));
         LIFE_CUDA_TRY(cudaMemsetAsync(rv.p, 0, sizeof(uint32_t), s));
         if (L.vbytes == 4)
-            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<float>(), m, rv.as<uint32_t>());
+            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.soff.as<uint16_t>(), L.val.as<float>(), m, rv.as<uint32_t>());
         else
-            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.fl.as<uint16_t>(), L.val.as<__nv_bfloat16>(), m,
+            run_vmax_kernel<<<grid1d(m), 256, 0, s>>>(L.soff.as<uint16_t>(), L.val.as<__nv_bfloat16>(), m,
                                                       rv.as<uint32_t>());
         LIFE_CHECK_LAUNCH();
         uint32_t bits = 0u;
@@ -919,6 +922,15 @@ __global__ void widen_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t 
         out[i] = __bfloat162float(in[i]);
 }
 
+// The exported form of the DSC stream's fascicle field: the brick-local fascicle
+// (the stream holds its byte offset in the weight table) | 0x8000 when the entry
+// continues the previous entry's (atom, row) (the stream keeps that bit in soff).
+__global__ void export_fl_kernel(const uint16_t* __restrict__ fl, const uint16_t* __restrict__ soff, int64_t n,
+                                 uint16_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (uint16_t)((fl[i] >> 2) | (soff[i] & CONT));
+}
+
 life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, int32_t* brick_tile_ptr,
                          int32_t* brick_fasc_ptr, int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
                          uint16_t* fl, float* val, cudaStream_t s) {
@@ -934,7 +946,10 @@ life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, 
     LIFE_TRY(cp(brick_fasc, L.brick_fasc, L.brick_fasc.bytes));
     LIFE_TRY(cp(brick_order, L.brick_order, sizeof(int32_t) * L.n_bricks));
     LIFE_TRY(cp(va, L.va, sizeof(uint16_t) * L.n_nnz));
-    LIFE_TRY(cp(fl, L.fl, sizeof(uint16_t) * L.n_nnz));
+    if (fl && L.n_nnz > 0) {
+        export_fl_kernel<<<grid1d(L.n_nnz), 256, 0, s>>>(L.fl.as<uint16_t>(), L.soff.as<uint16_t>(), L.n_nnz, fl);
+        LIFE_CHECK_LAUNCH();
+    }
     if (val && L.n_nnz > 0) {
         if (L.vbytes == 4) {
             LIFE_TRY(cp(val, L.val, sizeof(float) * L.n_nnz));
@@ -1179,10 +1194,11 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
 // the remainder in the stage's second half.
 template <bool SPLIT>
 __device__ __forceinline__ void store_s(unsigned char* S, uint32_t so, float s, float ss) {
+    // so: byte offset of the run's (row, atom) in the chunk (a run head: no CONT bit)
     const float x = s * ss;
     const __half h = __float2half_rn(x);
-    reinterpret_cast<__half*>(S)[so] = h;
-    if (SPLIT) reinterpret_cast<__half*>(S + DS_BYTES)[so] = __float2half_rn(f16_rest(x, h));
+    *reinterpret_cast<__half*>(S + so) = h;
+    if (SPLIT) *reinterpret_cast<__half*>(S + DS_BYTES + so) = __float2half_rn(f16_rest(x, h));
 }
 
 // S[a, row] for the runs that start inside this slot (a run = entries with the
@@ -1207,13 +1223,14 @@ __device__ __forceinline__ void dsc_runs(const SlotT& s, int base, int beg, int 
             const int idx = base + e;
             in = idx >= beg && idx < end;
         }
-        const uint32_t f = u16_at(s.fl, e);
-        const float t = in ? slot_val(s, e) * wl[f & 0x7FFFu] : 0.0f;
-        const bool head = in && !(f & CONT);
+        const uint32_t k = u16_at(s.key, e);  // S byte offset | CONT
+        const float t = in ? slot_val(s, e) * *reinterpret_cast<const float*>(
+                                 reinterpret_cast<const char*>(wl) + u16_at(s.fl, e)) : 0.0f;
+        const bool head = in && !(k & CONT);
         if (head && st.have) store_s<SPLIT>(S, st.so, st.cs, ss);   // the previous run ends here
         st.lead += (!st.have && !head) ? t : 0.0f;       // continuation of a run owned by the lane before
         st.cs = head ? t : st.cs + t;
-        st.so = head ? u16_at(s.key, e) : st.so;
+        st.so = head ? k : st.so;
         st.have = st.have || head;
     }
     st.head_seen = st.have;
@@ -1236,9 +1253,9 @@ __device__ __forceinline__ void dsc_slot(const TcArgs& A, const SlotT& s, int ba
                 st.cs += nlead;
             } else {
                 for (int j = j0; j < end; ++j) {
-                    const uint32_t f = A.fl[j];
-                    if (!(f & CONT)) break;
-                    st.cs += stream_val(A, s, j) * wl[f & 0x7FFFu];
+                    if (!(A.soff[j] & CONT)) break;
+                    st.cs += stream_val(A, s, j) * *reinterpret_cast<const float*>(
+                                                       reinterpret_cast<const char*>(wl) + A.fl[j]);
                 }
             }
         }
