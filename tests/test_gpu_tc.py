@@ -372,3 +372,31 @@ def test_tc_operand_scales(life, scale):
                             nt, nv, nf)
     assert (np.abs(g - g_ref) <= gb + fxb + 1e-38).all()
     assert rel(y, y_ref) <= TOL_BF16 and rel(g, g_ref) <= TOL_BF16
+
+
+def test_tc_dsc_non_finite_weights(life):
+    """Weights of order 1e6 (run sums far beyond FP16's range unless scaled) with
+    one +inf and one NaN: the FP16 scale of S comes from the finite weights, so
+    every output the non-finite weights do not reach stays within the rounding
+    bound, and the outputs they reach are non-finite exactly where the FP64
+    oracle's are (NaN where it has NaN)."""
+    p, D32, phi, idx = tiny_case(life)
+    nt, nv, nf = p.n_theta, p.n_voxels, p.n_fasc
+    rng = np.random.default_rng(41)
+    w = (rng.random(nf) * 1e6).astype(np.float32)
+    used = np.unique(phi.fasc)
+    w[int(used[2])] = np.inf
+    w[int(used[-3])] = np.nan
+    y, _ = life.life_dsc(idx, dev(D32), dev(w))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    y = y.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        y_ref = oracle.dsc(phi, D32, w.astype(np.float64), nt, nv)
+    np.testing.assert_array_equal(np.isfinite(y), np.isfinite(y_ref))
+    assert np.isnan(y[np.isnan(y_ref)]).all()
+    ok = np.isfinite(y_ref)
+    assert 0 < (~ok).sum() < ok.size
+    w0 = np.where(np.isfinite(w), w, 0.0).astype(np.float32)
+    yb, _ = rounding_bounds(phi, D32, w0, np.zeros(nt * nv, np.float32), nt, nv, nf)
+    assert (np.abs(y[ok] - y_ref[ok]) <= yb[ok] + 1e-30).all()

@@ -398,3 +398,33 @@ def test_tc32_autotune(life):
     info = idx.info()
     assert info["tuned"] == 1 and info["algo"] == life.LIFE_ALGO_TC and info["wc_groups"] in (1, 2, 4)
     run_check(life, idx, phi, D32, p.n_theta, p.n_atoms, p.n_voxels, p.n_fasc, seed=9)
+
+
+def test_tc32_dsc_non_finite_weights(life):
+    """As for BF16 storage: weights of order 1e6 with one +inf and one NaN; the
+    finite outputs keep the FP32 bound, the non-finite ones match the oracle's
+    (an infinite one may read NaN)."""
+    p = synth.config_problem("tiny")
+    D32 = oracle.dictionary(p.grad_dirs, p.atom_dirs, p.bval, p.lam)[0].astype(np.float32)
+    phi = oracle.canon(p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_atoms, p.n_voxels, p.n_fasc)
+    idx = tc32_index(life, p.coo_atom, p.coo_voxel, p.coo_fasc, p.coo_val, p.n_theta, p.n_atoms, p.n_voxels,
+                     p.n_fasc, ijk=p.voxel_ijk)
+    nt, nv, nf = p.n_theta, p.n_voxels, p.n_fasc
+    rng = np.random.default_rng(42)
+    w = (rng.random(nf) * 1e6).astype(np.float32)
+    used = np.unique(phi.fasc)
+    w[int(used[2])] = np.inf
+    w[int(used[-3])] = np.nan
+    y, _ = life.life_dsc(idx, dev(D32), dev(w))
+    torch.cuda.synchronize()
+    life.life_check_device_status()
+    y = y.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        y_ref = oracle.dsc(phi, D32, w.astype(np.float64), nt, nv)
+    np.testing.assert_array_equal(np.isfinite(y), np.isfinite(y_ref))
+    assert np.isnan(y[np.isnan(y_ref)]).all()
+    ok = np.isfinite(y_ref)
+    assert 0 < (~ok).sum() < ok.size
+    w0 = np.where(np.isfinite(w), w, 0.0).astype(np.float32)
+    yb = dsc_bound(phi, D32, w0, nt, nv, p.n_atoms)
+    assert (np.abs(y[ok] - y_ref[ok]) <= yb[ok] + 1e-30).all()
