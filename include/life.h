@@ -176,9 +176,10 @@ LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, 
  * that of the full stream up to the association of FP32 run sums.
  * Precision on a TC index with BF16 storage: Phi values and D are stored in BF16;
  * the tensor cores read D and S = Σ val·w as FP16 under exact power-of-two scales
- * (D's from its largest value, S's from max |w| and the largest run of Phi
- * values), FP32 accumulation.  A run sum more than ~2^40 below the largest
- * possible one in the call underflows FP16 and contributes zero.
+ * (D's from its largest value, S's from the largest finite |w| and the largest
+ * run of Phi values), FP32 accumulation.  A run sum more than ~2^40 below the
+ * largest possible one in the call underflows FP16 and contributes zero; a
+ * non-finite weight makes its run sums non-finite and leaves the others scaled.
  * With FP32 storage (precision LIFE_FP32, algo LIFE_ALGO_TC; Na <= 384): Phi
  * values stay FP32, S is summed in FP32, and D·2^kD and S·2^kS are each split into
  * FP16 hi and lo parts; Y = D_hi·S_hi + D_hi·S_lo + D_lo·S_hi (FP32 accumulation)
