@@ -83,7 +83,8 @@ typedef struct {
     int64_t device_bytes;  /* device memory held by the index */
     int64_t stream_bytes;  /* bytes of Phi one SpMV streams from memory */
     int64_t n_brick_fasc;  /* TC path: total entries of the brick-local fascicle tables */
-    int32_t n_sub;         /* TC path: 32-atom sub-chunks per tile */
+    int32_t n_sub;         /* TC path: Na padded to 128, / 32 (WC segments per tile row quarter;
+                              n_sub / 4 DSC chunks of 128 atoms per tile) */
     int32_t brick_edge;    /* TC path: spatial brick edge in voxels (0 = runs of voxel ids, when no
                               coordinates were given) */
     int32_t wc_groups;     /* TC path: WC scatter groups the next WC launch uses */
@@ -146,7 +147,10 @@ LIFE_API life_status life_index_export_voxel_streams(life_index idx, int32_t* vo
  * Copies the tensor-core layout (TC path only; LIFE_ENOTSUP otherwise), for
  * bit-exact tests of the restructuring.  Sizes come from life_index_get_info:
  *  tile_vox [n_tiles·128]        voxel of each tile row, -1 for padding rows
- *  sub_ptr [n_tiles·n_sub + 1]   entry offsets of each (tile, 32-atom sub-chunk)
+ *  chunk_ptr [n_tiles·n_sub/4 + 1]  entry offsets of each (tile, 128-atom chunk); inside a
+ *                                chunk the entries are ordered by cell (atom, row) in the
+ *                                order (row/8, atom mod 128 / 8, row mod 8, atom mod 8),
+ *                                then by fascicle
  *  brick_tile_ptr [n_bricks+1]   tiles of brick b: [ptr[b], ptr[b+1])
  *  brick_fasc_ptr [n_bricks+1], brick_fasc [n_brick_fasc]  brick-local fascicle tables
  *  brick_order [n_bricks]        processing order
@@ -154,7 +158,7 @@ LIFE_API life_status life_index_export_voxel_streams(life_index idx, int32_t* vo
  *  val [nnz]                     stored values as float32 (BF16 storage: widened; FP32: as stored)
  * Device outputs; any may be NULL.  Synchronizes `stream`.
  */
-LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* sub_ptr,
+LIFE_API life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* chunk_ptr,
                                              int32_t* brick_tile_ptr, int32_t* brick_fasc_ptr,
                                              int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
                                              uint16_t* fl, float* val, void* stream);

@@ -253,7 +253,7 @@ def life_index_export_tiles(index: LifeIndex) -> dict:
     dev = torch.device("cuda")
     nt, nb, m = i["n_tiles"], i["n_bricks"], i["nnz"]
     out = dict(tile_vox=torch.empty(nt * 128, dtype=torch.int32, device=dev),
-               sub_ptr=torch.empty(nt * i["n_sub"] + 1, dtype=torch.int32, device=dev),
+               chunk_ptr=torch.empty(nt * (i["n_sub"] // 4) + 1, dtype=torch.int32, device=dev),
                brick_tile_ptr=torch.empty(nb + 1, dtype=torch.int32, device=dev),
                brick_fasc_ptr=torch.empty(nb + 1, dtype=torch.int32, device=dev),
                brick_fasc=torch.empty(max(i["n_brick_fasc"], 1), dtype=torch.int32, device=dev),
@@ -262,7 +262,7 @@ def life_index_export_tiles(index: LifeIndex) -> dict:
                fl=torch.empty(max(m, 1), dtype=torch.int16, device=dev),
                val=torch.empty(max(m, 1), dtype=torch.float32, device=dev))
     _check(load().life_index_export_tiles(index.handle, *[_ptr(out[k]) for k in (
-        "tile_vox", "sub_ptr", "brick_tile_ptr", "brick_fasc_ptr", "brick_fasc", "brick_order", "va", "fl", "val")],
+        "tile_vox", "chunk_ptr", "brick_tile_ptr", "brick_fasc_ptr", "brick_fasc", "brick_order", "va", "fl", "val")],
         _stream()))
     return out
 

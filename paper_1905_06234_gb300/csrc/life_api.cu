@@ -231,7 +231,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
     const DevBuf* bufs[] = {&idx->ukey, &idx->uval, &idx->voxel_ijk, &idx->vox.vox_ptr, &idx->vox.atom,
                             &idx->vox.fasc, &idx->vox.val, &idx->atoml.voxel, &idx->atoml.fasc, &idx->atoml.val,
                             &idx->atoml.chunk_beg, &idx->atoml.chunk_atom, &idx->atoml.atom_chunk,
-                            &idx->tile.tile_vox, &idx->tile.sub_ptr, &idx->tile.brick_tile_ptr,
+                            &idx->tile.tile_vox, &idx->tile.chunk_ptr, &idx->tile.brick_tile_ptr,
                             &idx->tile.brick_fasc_ptr, &idx->tile.brick_fasc, &idx->tile.brick_order,
                             &idx->tile.va, &idx->tile.soff, &idx->tile.fl, &idx->tile.val, &idx->tile.wkey,
                             &idx->tile.wfl, &idx->tile.wval, &idx->tile.wseg_ptr, &idx->tile.wb_src,
@@ -243,7 +243,7 @@ extern "C" life_status life_index_get_info(life_index idx, life_index_info* out)
     I.device_bytes = tot;
     if (idx->algo == LIFE_ALGO_TC && idx->tile.built)
         I.stream_bytes = idx->tile.n_nnz * (4 + idx->tile.vbytes) +
-                         (int64_t)idx->tile.n_tiles * (TILE_V + idx->tile.n_sub) * 4;
+                         (int64_t)idx->tile.n_tiles * (TILE_V + idx->tile.kp / 128) * 4;
     else
         I.stream_bytes = idx->nnz * (2 + 4 + (idx->precision == LIFE_BF16 ? 2 : 4)) + 4 * ((int64_t)idx->nv + 1);
     if (idx->tile.built) {
@@ -274,7 +274,7 @@ extern "C" life_status life_index_export_voxel_streams(life_index idx, int32_t* 
     return export_voxel_streams(idx, vox_ptr, atom, fasc, val, (cudaStream_t)stream);
 }
 
-extern "C" life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* sub_ptr,
+extern "C" life_status life_index_export_tiles(life_index idx, int32_t* tile_vox, int32_t* chunk_ptr,
                                                int32_t* brick_tile_ptr, int32_t* brick_fasc_ptr, int32_t* brick_fasc,
                                                int32_t* brick_order, uint16_t* va, uint16_t* fl, float* val,
                                                void* stream) {
@@ -286,7 +286,7 @@ extern "C" life_status life_index_export_tiles(life_index idx, int32_t* tile_vox
         set_error("life_index_export_tiles: the index has no tensor-core layout");
         return LIFE_ENOTSUP;
     }
-    return export_tiles(idx, tile_vox, sub_ptr, brick_tile_ptr, brick_fasc_ptr, brick_fasc, brick_order, va, fl, val,
+    return export_tiles(idx, tile_vox, chunk_ptr, brick_tile_ptr, brick_fasc_ptr, brick_fasc, brick_order, va, fl, val,
                         (cudaStream_t)stream);
 }
 

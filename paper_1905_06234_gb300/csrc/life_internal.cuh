@@ -124,19 +124,21 @@ struct AtomLayout {
 };
 
 // TC path: spatial bricks of 128-voxel tiles with brick-local fascicle numbering.
-// Entries are sorted by (tile, atom, row, fascicle); sub_ptr splits each tile
-// into 32-atom sub-chunks.
+// The DSC stream is sorted by (tile, 128-atom chunk, cell, fascicle), the cells
+// (atom, row) of a chunk in the order of their byte offsets in the chunk's S operand
+// (8-row group, 8-atom group, row mod 8, atom mod 8); chunk_ptr splits each tile
+// into its chunks.
 struct TileLayout {
     bool built = false;
     int64_t n_tiles = 0, n_bricks = 0, n_nnz = 0;
     int32_t np = 0;          // Nθ padded to a multiple of 16 (MMA N or K)
-    int32_t kp = 0;          // Na padded to a multiple of 64 (MMA K or N)
-    int32_t n_sub = 0;       // kp / 32
+    int32_t kp = 0;          // Na padded to a multiple of 128 (whole DSC chunks; MMA K or N)
+    int32_t n_sub = 0;       // kp / 32: WC segments per tile and row quarter
     int32_t max_fb = 0;      // largest brick-local fascicle table
     int32_t brick_edge = 0;  // spatial brick edge used (0 = voxel-id groups)
     int32_t brick_b = 0;     // brick edge B used (also for voxel-id groups of B^3)
     DevBuf tile_vox;         // int32 [n_tiles * TILE_V] voxel id per tile row (-1 = padding)
-    DevBuf sub_ptr;          // int32 [n_tiles * n_sub + 1] entry offsets per (tile, 32-atom sub-chunk)
+    DevBuf chunk_ptr;        // int32 [n_tiles * kp / 128 + 1] DSC-stream entry offsets per (tile, 128-atom chunk)
     DevBuf brick_tile_ptr;   // int32 [n_bricks + 1] tiles of each brick (consecutive)
     DevBuf brick_fasc_ptr;   // int32 [n_bricks + 1] offsets into brick_fasc
     DevBuf brick_fasc;       // int32 [sum] global fascicle id of each brick-local fascicle
@@ -247,7 +249,7 @@ life_status build_voxel_layout(life_index_s* ix, const int32_t* atom, const int3
                                const int32_t* fasc, const float* val, cudaStream_t s);
 life_status build_atom_layout(life_index_s* ix, cudaStream_t s);
 life_status build_tile_layout(life_index_s* ix, cudaStream_t s);
-life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, int32_t* brick_tile_ptr,
+life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* chunk_ptr, int32_t* brick_tile_ptr,
                          int32_t* brick_fasc_ptr, int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
                          uint16_t* fl, float* val, cudaStream_t s);
 life_status export_voxel_streams(life_index_s* ix, int32_t* vox_ptr, int32_t* atom, int32_t* fasc,

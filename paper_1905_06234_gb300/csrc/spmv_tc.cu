@@ -25,7 +25,8 @@ namespace life {
 
 using namespace ptx;
 
-constexpr int SUB = 32;                  // atoms per sub-chunk (offset granularity)
+constexpr int SUB = 32;                  // atoms per WC segment (offset granularity of the WC streams)
+constexpr int DKC = 128;                 // atoms per DSC K chunk (offset granularity of the DSC stream)
 constexpr int ZW = 33;                   // row stride (floats) of a WC scatter warp's 32 x 32 Z tile
 constexpr uint16_t CONT = 0x8000;        // entry continues the previous entry's (atom, row)
 constexpr uint64_t WAIT_LIMIT = 2000000000ull; // ns before a wait gives up
@@ -46,7 +47,21 @@ static unsigned grid1d(int64_t n, int threads = 256) {
 
 // ============================================================ layout build
 
-// key = tile | atom | row | fascicle  (payload: position in the merged list)
+// The (atom, row) cell part (16 bits) of the DSC sort key: the 128-atom chunk,
+// then the cell's place in the chunk's S operand (8-row group, 8-atom group, row
+// mod 8, atom mod 8), i.e. the order of its byte offset there.  An 8 x 8 group of
+// cells spans the 32 shared-memory banks once, so the run sums that the lanes of a
+// warp store at the same time fall on more distinct banks than in (atom, row)
+// order.  Runs (entries of one cell) stay contiguous; Na < 512.
+__host__ __device__ inline uint64_t cell_key(uint64_t a, uint64_t row) {
+    return ((a >> 7) << 14) | ((row >> 3) << 10) | (((a >> 3) & 15u) << 6) | ((row & 7u) << 3) | (a & 7u);
+}
+__host__ __device__ inline void cell_of_key(uint64_t ck, uint32_t& a, uint32_t& row) {
+    a = (uint32_t)((((ck >> 14) & 3u) << 7) | (((ck >> 6) & 15u) << 3) | (ck & 7u));
+    row = (uint32_t)((((ck >> 10) & 15u) << 3) | ((ck >> 3) & 7u));
+}
+
+// key = tile | cell_key(atom, row) | fascicle  (payload: position in the merged list)
 __global__ void tile_key_kernel(const uint64_t* __restrict__ ukey, int64_t m, int sa, int sv, uint64_t amask,
                                 uint64_t fmask, int bf, const int32_t* __restrict__ vox_tile,
                                 const int32_t* __restrict__ vox_row, uint64_t* __restrict__ key,
@@ -55,7 +70,7 @@ __global__ void tile_key_kernel(const uint64_t* __restrict__ ukey, int64_t m, in
         const uint64_t k = ukey[i];
         const uint64_t v = k >> sv, a = (k >> sa) & amask, f = k & fmask;
         const uint64_t t = (uint64_t)vox_tile[v], row = (uint64_t)vox_row[v];
-        key[i] = (t << (16 + bf)) | (a << (7 + bf)) | (row << bf) | f;
+        key[i] = (t << (16 + bf)) | (cell_key(a, row) << bf) | f;
         pay[i] = (uint32_t)i;
     }
 }
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, 8) wb_gather_live_kernel(const
 }
 
 struct CompactArgs {
-    const int32_t* sub_ptr;
+    const int32_t* chunk_ptr;
     const int32_t* tile_brick;
     const int32_t* wb_ptr;
     const float* wb;
@@ -293,7 +308,7 @@ struct CompactArgs {
     __nv_bfloat16* c_val;
     int32_t* c_chunk_end;   // [n_tiles * chunks per tile] end of each chunk's live entries
     SparseCtl* ctl;
-    int n_sub, n_c;         // sub-chunks and 128-atom chunks per tile
+    int n_c;                // 128-atom chunks per tile
     int64_t n_chunks, wb_total;
 };
 
@@ -332,9 +347,9 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_rebuild_kernel(CompactArgs C)
     const uint32_t below = (1u << lane) - 1u;
     const int64_t warps = (int64_t)gridDim.x * (CMP_THREADS / 32);
     for (int64_t ch = blockIdx.x * (int64_t)(CMP_THREADS / 32) + (threadIdx.x >> 5); ch < C.n_chunks; ch += warps) {
-        const int64_t t = ch / C.n_c, c = ch - t * C.n_c;
+        const int64_t t = ch / C.n_c;
         const float* wbb = C.wb + C.wb_ptr[C.tile_brick[t]];
-        const int beg = C.sub_ptr[t * C.n_sub + c * (128 / SUB)], end = C.sub_ptr[t * C.n_sub + (c + 1) * (128 / SUB)];
+        const int beg = C.chunk_ptr[ch], end = C.chunk_ptr[ch + 1];
         int out = beg;
         uint32_t prev = 0xFFFFFFFFu;  // S offset of the last live entry so far (none)
         for (int base = (beg & ~7) + lane * 8; __any_sync(0xffffffffu, base < end); base += 256) {
@@ -430,31 +445,33 @@ __device__ __forceinline__ void store_val(float* p, float x) { *p = x; }
 __device__ __forceinline__ float load_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float load_val(const float* p) { return *p; }
 
-// Entry streams in tile order, the continuation flag, and the sub-chunk offsets.
+// Entry streams in tile order, the continuation flag, and the chunk offsets.
 template <class VT>
 __global__ void tile_stream_kernel(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ spay, int64_t m,
-                                   int bf, const float* __restrict__ uval, int32_t n_sub, int64_t n_segs,
+                                   int bf, const float* __restrict__ uval, int32_t n_c, int64_t n_segs,
                                    uint16_t* __restrict__ va, uint16_t* __restrict__ soff,
                                    uint16_t* __restrict__ fl, VT* __restrict__ val,
-                                   int32_t* __restrict__ sub_ptr) {
+                                   int32_t* __restrict__ chunk_ptr) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = skey[j];
         const uint64_t t = k >> (16 + bf);
-        const uint32_t a = (uint32_t)((k >> (7 + bf)) & 511u), row = (uint32_t)((k >> bf) & 127u);
+        uint32_t a, row;
+        cell_of_key((k >> bf) & 0xFFFFu, a, row);
         va[j] = (uint16_t)(row | (a << 7));
         // byte offset of (row, atom) in an S chunk (< 32768), with the continuation bit
         const bool cont = j > 0 && (skey[j - 1] >> bf) == (k >> bf);
         soff[j] = (uint16_t)(ptx::kmajor_off(row, a & 127u, (128 / 8) * 128) | (cont ? CONT : 0u));
         store_val(val + j, uval[spay[j]]);
-        const int64_t seg = (int64_t)t * n_sub + (a >> 5);
+        // the chunk is the top of the cell key
+        const int64_t seg = (int64_t)t * n_c + (a >> 7);
         int64_t segp = -1;
         if (j > 0) {
             const uint64_t kp = skey[j - 1];
-            segp = (int64_t)(kp >> (16 + bf)) * n_sub + (int64_t)(((kp >> (7 + bf)) & 511u) >> 5);
+            segp = (int64_t)(kp >> (16 + bf)) * n_c + (int64_t)((kp >> (14 + bf)) & 3u);
         }
-        for (int64_t q = segp + 1; q <= seg; ++q) sub_ptr[q] = (int32_t)j;
+        for (int64_t q = segp + 1; q <= seg; ++q) chunk_ptr[q] = (int32_t)j;
         if (j == m - 1)
-            for (int64_t q = seg + 1; q <= n_segs; ++q) sub_ptr[q] = (int32_t)m;
+            for (int64_t q = seg + 1; q <= n_segs; ++q) chunk_ptr[q] = (int32_t)m;
     }
 }
 
@@ -465,7 +482,9 @@ __global__ void wc_key_kernel(const uint64_t* __restrict__ skey, int64_t m, int 
     const uint64_t fmask = (1ull << bf) - 1;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = skey[j];
-        const uint64_t t = k >> (16 + bf), a = (k >> (7 + bf)) & 511u, row = (k >> bf) & 127u;
+        uint32_t a32, r32;
+        cell_of_key((k >> bf) & 0xFFFFu, a32, r32);
+        const uint64_t t = k >> (16 + bf), a = a32, row = r32;
         key3[j] = (t << (16 + bf)) | ((row >> 5) << (14 + bf)) | (a << (5 + bf)) | ((row & 31u) << bf) | (k & fmask);
         pay3[j] = (uint32_t)j;
     }
@@ -773,7 +792,8 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
             bp[b] = ix->batch.vox_group[H.tile_vox[(size_t)H.brick_tile_ptr[b] * TILE_V]];
         LIFE_TRY(upload(ix->batch.brick_prob, bp, s));
     }
-    const int64_t n_segs = H.n_tiles * L.n_sub;
+    const int n_c = L.kp / DKC;  // 128-atom chunks per tile
+    const int64_t n_segs = H.n_tiles * n_c;
     // streams padded to whole 8-entry slots (the kernels load 16 bytes at a time)
     const int64_t m_pad = (m + 7) / 8 * 8 + 8;
     LIFE_TRY(L.va.alloc(sizeof(uint16_t) * m_pad));
@@ -784,7 +804,7 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     LIFE_CUDA_TRY(cudaMemsetAsync(L.soff.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.fl.p, 0, sizeof(uint16_t) * m_pad, s));
     LIFE_CUDA_TRY(cudaMemsetAsync(L.val.p, 0, (size_t)L.vbytes * m_pad, s));
-    LIFE_TRY(L.sub_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
+    LIFE_TRY(L.chunk_ptr.alloc(sizeof(int32_t) * (n_segs + 1)));
     if (m > 0) {
         local_fasc_kernel<<<grid1d(m), 256, 0, s>>>(key2.as<uint64_t>(), pay2.as<uint32_t>(), m, bf,
                                                     head.as<int32_t>(), uidx.as<int32_t>(), L.brick_fasc_ptr.as<int32_t>(),
@@ -792,17 +812,17 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
         LIFE_CHECK_LAUNCH();
         if (L.vbytes == 4)
             tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
-                                                         ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                         ix->uval.as<float>(), n_c, n_segs, L.va.as<uint16_t>(),
                                                          L.soff.as<uint16_t>(), L.fl.as<uint16_t>(), L.val.as<float>(),
-                                                         L.sub_ptr.as<int32_t>());
+                                                         L.chunk_ptr.as<int32_t>());
         else
             tile_stream_kernel<<<grid1d(m), 256, 0, s>>>(skey.as<uint64_t>(), spay.as<uint32_t>(), m, bf,
-                                                         ix->uval.as<float>(), L.n_sub, n_segs, L.va.as<uint16_t>(),
+                                                         ix->uval.as<float>(), n_c, n_segs, L.va.as<uint16_t>(),
                                                          L.soff.as<uint16_t>(), L.fl.as<uint16_t>(),
-                                                         L.val.as<__nv_bfloat16>(), L.sub_ptr.as<int32_t>());
+                                                         L.val.as<__nv_bfloat16>(), L.chunk_ptr.as<int32_t>());
         LIFE_CHECK_LAUNCH();
     } else {
-        fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.sub_ptr.as<int32_t>(), n_segs + 1, 0);
+        fill_kernel<<<grid1d(n_segs + 1), 256, 0, s>>>(L.chunk_ptr.as<int32_t>(), n_segs + 1, 0);
         LIFE_CHECK_LAUNCH();
     }
     L.run_vmax = 0.0f;
@@ -900,9 +920,9 @@ life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     std::vector<int32_t> tptr(H.n_tiles + 1);
     {
         std::vector<int32_t> sp(n_segs + 1);
-        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.sub_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.chunk_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
         LIFE_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int64_t t = 0; t <= H.n_tiles; ++t) tptr[t] = sp[t * L.n_sub];
+        for (int64_t t = 0; t <= H.n_tiles; ++t) tptr[t] = sp[t * n_c];
     }
     std::vector<int64_t> bnnz(H.n_bricks);
     for (int64_t b = 0; b < H.n_bricks; ++b)
@@ -931,7 +951,7 @@ __global__ void export_fl_kernel(const uint16_t* __restrict__ fl, const uint16_t
         out[i] = (uint16_t)((fl[i] >> 2) | (soff[i] & CONT));
 }
 
-life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, int32_t* brick_tile_ptr,
+life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* chunk_ptr, int32_t* brick_tile_ptr,
                          int32_t* brick_fasc_ptr, int32_t* brick_fasc, int32_t* brick_order, uint16_t* va,
                          uint16_t* fl, float* val, cudaStream_t s) {
     TileLayout& L = ix->tile;
@@ -940,7 +960,7 @@ life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, 
         return LIFE_OK;
     };
     LIFE_TRY(cp(tile_vox, L.tile_vox, sizeof(int32_t) * L.n_tiles * TILE_V));
-    LIFE_TRY(cp(sub_ptr, L.sub_ptr, sizeof(int32_t) * (L.n_tiles * L.n_sub + 1)));
+    LIFE_TRY(cp(chunk_ptr, L.chunk_ptr, sizeof(int32_t) * (L.n_tiles * (L.kp / DKC) + 1)));
     LIFE_TRY(cp(brick_tile_ptr, L.brick_tile_ptr, sizeof(int32_t) * (L.n_bricks + 1)));
     LIFE_TRY(cp(brick_fasc_ptr, L.brick_fasc_ptr, sizeof(int32_t) * (L.n_bricks + 1)));
     LIFE_TRY(cp(brick_fasc, L.brick_fasc, L.brick_fasc.bytes));
@@ -966,7 +986,7 @@ life_status export_tiles(life_index_s* ix, int32_t* tile_vox, int32_t* sub_ptr, 
 
 struct TcArgs {
     const int32_t* tile_vox;
-    const int32_t* sub_ptr;
+    const int32_t* chunk_ptr;  // DSC stream: entries of (tile t, chunk c) from chunk_ptr[t·n_c + c]
     const int32_t* brick_tile_ptr;
     const int32_t* brick_fasc_ptr;
     const int32_t* brick_fasc;
@@ -1093,12 +1113,12 @@ __device__ __forceinline__ float stream_val(const TcArgs& A, const EntrySlot&, i
 
 __device__ __forceinline__ float stream_val(const TcArgs& A, const EntrySlot32&, int j) { return A.val32[j]; }
 
-__device__ __forceinline__ int chunk_beg(const TcArgs& A, int t, int c, int subs_per_chunk) {
-    return A.sub_ptr[(int64_t)t * A.n_sub + (int64_t)c * subs_per_chunk];
+__device__ __forceinline__ int chunk_beg(const TcArgs& A, int t, int c, int n_c) {
+    return A.chunk_ptr[(int64_t)t * n_c + c];
 }
 
-__device__ __forceinline__ int chunk_end(const TcArgs& A, int t, int c, int subs_per_chunk, int n_c) {
-    return A.chunk_end ? A.chunk_end[(int64_t)t * n_c + c] : chunk_beg(A, t, c + 1, subs_per_chunk);
+__device__ __forceinline__ int chunk_end(const TcArgs& A, int t, int c, int n_c) {
+    return A.chunk_end ? A.chunk_end[(int64_t)t * n_c + c] : A.chunk_ptr[(int64_t)t * n_c + c + 1];
 }
 
 // Advances (r, brick, t, c) to the CTA's next chunk; false when none is left.
@@ -1145,7 +1165,6 @@ constexpr int DSC_EPI_WARPS = 4;
 constexpr int DSC_MMA_WARP = DSC_PROD_WARPS + DSC_EPI_WARPS;
 constexpr int DSC_THREADS = (DSC_MMA_WARP + 1) * 32;
 constexpr int DSC_PROD_THREADS = DSC_PROD_WARPS * 32;
-constexpr int DKC = 128;                                  // atoms per DSC K chunk
 constexpr int DSTAGE = 2;                                 // S-chunk ring depth
 constexpr uint32_t DS_BYTES = TILE_V * DKC * 2;           // one S chunk: 128 rows x 128 atoms, bf16
 constexpr uint32_t DS_SBO = (DKC / 8) * 128;              // 8-row group stride of an S chunk
@@ -1455,7 +1474,6 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
     const uint32_t tb = tmem_base;
     const int G = gridDim.x, cta = blockIdx.x;
     const int n_c = A.kp / DKC;
-    const int spc = DKC / SUB;  // sub-chunks per chunk
     double sq = 0.0;
 
     if (F32 && warp < DSC_MMA_WARP) {
@@ -1491,7 +1509,7 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
         const int b0 = live_brick(A, G, cta, r);
         if (b0 >= 0) {
             int brick = b0, t = A.brick_tile_ptr[brick], c = 0;
-            int beg = chunk_beg(A, t, 0, spc), end = chunk_end(A, t, 0, spc, n_c);
+            int beg = chunk_beg(A, t, 0, n_c), end = chunk_end(A, t, 0, n_c);
             int base = (beg & ~7) + tid * SLOT;
             bool have = base < end;
             SlotT cur{};
@@ -1559,8 +1577,8 @@ __global__ void __maxnreg__(72) dsc_tc_kernel(TcArgs A) {
                 const bool nvalid = next_chunk(A, G, cta, n_c, nr, nbrick, nt, nc, nnew);
                 int nbeg = 0, nend = 0;
                 if (nvalid) {
-                    nbeg = chunk_beg(A, nt, nc, spc);
-                    nend = chunk_end(A, nt, nc, spc, n_c);
+                    nbeg = chunk_beg(A, nt, nc, n_c);
+                    nend = chunk_end(A, nt, nc, n_c);
                 }
                 const int nbase = (nbeg & ~7) + tid * SLOT;
                 const bool nhave = nvalid && nbase < nend;
@@ -2773,7 +2791,7 @@ static TcArgs make_args(life_index_s* ix) {
     TileLayout& L = ix->tile;
     TcArgs A{};
     A.tile_vox = L.tile_vox.as<int32_t>();
-    A.sub_ptr = L.sub_ptr.as<int32_t>();
+    A.chunk_ptr = L.chunk_ptr.as<int32_t>();
     A.brick_tile_ptr = L.brick_tile_ptr.as<int32_t>();
     A.brick_fasc_ptr = L.brick_fasc_ptr.as<int32_t>();
     A.brick_fasc = L.brick_fasc.as<int32_t>();
@@ -2858,7 +2876,7 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
     SparseCtl* ctl = L.sparse_ctl.as<SparseCtl>();
     if (!(gate && gate_mode == GATE_ACTIVE)) {
         CompactArgs C{};
-        C.sub_ptr = L.sub_ptr.as<int32_t>();
+        C.chunk_ptr = L.chunk_ptr.as<int32_t>();
         C.tile_brick = L.tile_brick.as<int32_t>();
         C.wb_ptr = L.wb_ptr.as<int32_t>();
         C.wb = L.wb.as<float>();
@@ -2871,7 +2889,6 @@ life_status dsc_tc(life_index_s* ix, const float* D, const float* w, const float
         C.c_val = L.c_val.as<__nv_bfloat16>();
         C.c_chunk_end = L.c_chunk_end.as<int32_t>();
         C.ctl = ctl;
-        C.n_sub = L.n_sub;
         C.n_c = L.kp / DKC;
         C.n_chunks = L.n_tiles * C.n_c;
         C.wb_total = L.wb_total;
@@ -2939,17 +2956,17 @@ life_status sparse_stats(life_index_s* ix, int64_t* out, cudaStream_t s) {
     if (!L.built || !L.sparse) return LIFE_OK;
     SparseCtl c{};
     const int n_c = L.kp / DKC;
-    std::vector<int32_t> ends((size_t)(L.n_tiles * n_c)), sp((size_t)(L.n_tiles * L.n_sub + 1));
+    std::vector<int32_t> ends((size_t)(L.n_tiles * n_c)), sp((size_t)(L.n_tiles * n_c + 1));
     LIFE_CUDA_TRY(cudaMemcpyAsync(&c, L.sparse_ctl.p, sizeof(SparseCtl), cudaMemcpyDeviceToHost, s));
     if (!ends.empty()) {
         LIFE_CUDA_TRY(cudaMemcpyAsync(ends.data(), L.c_chunk_end.p, sizeof(int32_t) * ends.size(),
                                       cudaMemcpyDeviceToHost, s));
-        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.sub_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
+        LIFE_CUDA_TRY(cudaMemcpyAsync(sp.data(), L.chunk_ptr.p, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost, s));
     }
     LIFE_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t ncmp = 0;
     for (int64_t t = 0; t < L.n_tiles; ++t)
-        for (int c2 = 0; c2 < n_c; ++c2) ncmp += ends[t * n_c + c2] - sp[t * L.n_sub + c2 * (DKC / SUB)];
+        for (int c2 = 0; c2 < n_c; ++c2) ncmp += ends[t * n_c + c2] - sp[t * n_c + c2];
     out[0] = (int64_t)c.n_calls;
     out[1] = (int64_t)c.n_compact_calls;
     out[2] = (int64_t)c.n_compactions;

@@ -210,7 +210,10 @@ def expected_tiles(phi, tile_vox, brick_tile_ptr, nv, n_sub):
     row = vox_row[phi.voxel]
     a = phi.atom.astype(np.int64)
     f = phi.fasc.astype(np.int64)
-    order = np.lexsort((f, row, a, t))
+    # inside a 128-atom chunk, cells in the order of their place in the S operand:
+    # (row / 8, atom mod 128 / 8, row mod 8, atom mod 8)
+    cell = ((a >> 7) << 14) | ((row >> 3) << 10) | (((a >> 3) & 15) << 6) | ((row & 7) << 3) | (a & 7)
+    order = np.lexsort((f, cell, t))
     t, row, a, f, val = t[order], row[order], a[order], f[order], phi.val[order]
     va = (row | (a << 7)).astype(np.uint16)
     b = tile_brick[t]
@@ -220,12 +223,13 @@ def expected_tiles(phi, tile_vox, brick_tile_ptr, nv, n_sub):
     cont = np.zeros(len(t), bool)
     cont[1:] = (t[1:] == t[:-1]) & (a[1:] == a[:-1]) & (row[1:] == row[:-1])
     fl = (local | np.where(cont, 0x8000, 0)).astype(np.uint16)
-    seg = t * n_sub + (a >> 5)
-    sub_ptr = np.searchsorted(seg, np.arange(n_tiles * n_sub + 1))
+    n_c = n_sub // 4
+    seg = t * n_c + (a >> 7)
+    chunk_ptr = np.searchsorted(seg, np.arange(n_tiles * n_c + 1))
     import torch as _t
     valb = _t.from_numpy(val).to(_t.bfloat16).float().numpy()
     return dict(va=va, fl=fl, val=valb, brick_fasc_ptr=bptr.astype(np.int32), brick_fasc=(bfk & 0xffffffff).astype(np.int32),
-                sub_ptr=sub_ptr.astype(np.int32))
+                chunk_ptr=chunk_ptr.astype(np.int32))
 
 
 @pytest.mark.parametrize("use_ijk", [False, True])
@@ -238,7 +242,7 @@ def test_tc_layout_bit_exact(life, use_ijk):
     got = {k: v.cpu().numpy() for k, v in life.life_index_export_tiles(idx).items()}
     m = info["nnz"]
     exp = expected_tiles(phi, got["tile_vox"], got["brick_tile_ptr"], p.n_voxels, info["n_sub"])
-    np.testing.assert_array_equal(got["sub_ptr"], exp["sub_ptr"])
+    np.testing.assert_array_equal(got["chunk_ptr"], exp["chunk_ptr"])
     np.testing.assert_array_equal(got["va"][:m].view(np.uint16), exp["va"])
     np.testing.assert_array_equal(got["val"][:m], exp["val"])
     np.testing.assert_array_equal(got["brick_fasc_ptr"], exp["brick_fasc_ptr"])

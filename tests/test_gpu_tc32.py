@@ -191,7 +191,7 @@ def test_tc32_layout_values_are_fp32(life):
     m = idx.info()["nnz"]
     tile_vox = t["tile_vox"]
     va = t["va"][:m].view(np.uint16).astype(np.int64)
-    tile = np.repeat(np.arange(len(t["sub_ptr"]) - 1) // idx.info()["n_sub"], np.diff(t["sub_ptr"]))
+    tile = np.repeat(np.arange(len(t["chunk_ptr"]) - 1) // (idx.info()["n_sub"] // 4), np.diff(t["chunk_ptr"]))
     vox = tile_vox[tile * 128 + (va & 127)]
     atom = va >> 7
     # each (voxel, atom) cell's values, as a multiset, are the oracle's merged ones
