@@ -321,7 +321,11 @@ LIFE_API life_status life_sbb_state_init(life_sbb_state* st, void* stream);
  * Vectors are float32; every dot product, alpha and the test are FP64.
  *  b   float32 [Nθ·Nv];  w float32 [Nf] (updated in place);  st device state;
  *  workspace  device, life_sbb_workspace_bytes() bytes, 256-byte aligned.
- * A converged state makes the call a no-op.
+ * A converged state makes the call a no-op.  The iteration's kernels are launched
+ * as one graph, captured on the first call for a given (D, b, w, st, workspace,
+ * tol, eq7_on_even) and replayed after that; on a stream that is being captured
+ * they are launched one by one instead.  Rebuilding the index's layout
+ * (life_index_autotune) drops the cached graphs.
  */
 LIFE_API life_status life_sbbnnls_step(life_index idx, const float* D, const float* b, float* w,
                               life_sbb_state* st, void* workspace, double tol, int32_t eq7_on_even,

@@ -185,6 +185,7 @@ static life_status autotune_simt(life_index_s* ix, cudaStream_t s) {
     }
     ix->simt_runs = (t_dsc[1] < t_dsc[0] ? SIMT_RUNS_DSC : 0) | (t_wc[1] < t_wc[0] ? SIMT_RUNS_WC : 0);
     LIFE_CUDA_TRY(cudaStreamSynchronize(s));
+    drop_index_graphs(ix);  // cached graphs hold the kernel choice
     ix->tuned = 1;
     return LIFE_OK;
 }

@@ -42,6 +42,8 @@ int device_sm_count() {
 size_t sbb_workspace_bytes(const life_index_s* ix);
 life_status sbb_enqueue_step(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
                              void* workspace, double tol, int eq7_on_even, cudaStream_t s);
+life_status build_step_graph(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
+                             void* ws, double tol, int eq7, cudaGraphExec_t* out);
 
 static bool use_tc(const life_index_s* ix) { return ix->algo == LIFE_ALGO_TC && ix->tile.built; }
 
@@ -205,6 +207,7 @@ extern "C" life_status life_index_free(life_index idx) {
     if (!idx) return LIFE_OK;
     cudaDeviceSynchronize();
     if (idx->graph) cudaGraphExecDestroy(idx->graph);
+    if (idx->step_graph) cudaGraphExecDestroy(idx->step_graph);
     delete idx;
     return LIFE_OK;
 }
@@ -363,7 +366,29 @@ extern "C" life_status life_sbbnnls_step(life_index idx, const float* D, const f
                                          life_sbb_state* st, void* workspace, double tol, int32_t eq7_on_even,
                                          void* stream) {
     LIFE_TRY(check_sbb_args(idx, D, b, w, st, workspace, "life_sbbnnls_step"));
-    return sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    // inside the caller's own stream capture: the kernels themselves
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return sbb_enqueue_step(idx, D, b, w, st, workspace, tol, eq7_on_even, s);
+    }
+    // otherwise the step's launches as one cached graph (one launch call per step)
+    const void* key[8] = {D, b, w, st, workspace, nullptr, nullptr, nullptr};
+    const bool same = idx->step_graph && idx->step_tol == tol && idx->step_eq7 == eq7_on_even &&
+                      std::memcmp(key, idx->step_key, sizeof(key)) == 0;
+    if (!same) {
+        if (idx->step_graph) {
+            cudaGraphExecDestroy(idx->step_graph);
+            idx->step_graph = nullptr;
+        }
+        LIFE_TRY(build_step_graph(idx, D, b, w, st, workspace, tol, eq7_on_even, &idx->step_graph));
+        std::memcpy(idx->step_key, key, sizeof(key));
+        idx->step_tol = tol;
+        idx->step_eq7 = eq7_on_even;
+    }
+    LIFE_CUDA_TRY(cudaGraphLaunch(idx->step_graph, s));
+    return LIFE_OK;
 }
 
 namespace life {
@@ -442,6 +467,41 @@ life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s) {
 }  // namespace life
 
 namespace life {
+
+void drop_index_graphs(life_index_s* ix) {
+    if (!ix->graph && !ix->step_graph) return;
+    cudaDeviceSynchronize();  // a launch of either may still be running
+    if (ix->graph) cudaGraphExecDestroy(ix->graph);
+    if (ix->step_graph) cudaGraphExecDestroy(ix->step_graph);
+    ix->graph = nullptr;
+    ix->step_graph = nullptr;
+}
+
+// One SBB iteration captured on a private stream and instantiated.
+life_status build_step_graph(life_index_s* ix, const float* D, const float* b, float* w, life_sbb_state* st,
+                             void* ws, double tol, int eq7, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaStream_t cap;
+    LIFE_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    life_status est = LIFE_OK;
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        est = sbb_enqueue_step(ix, D, b, w, st, ws, tol, eq7, cap);
+        cudaError_t le = cudaGetLastError();
+        ce = cudaStreamEndCapture(cap, &g);
+        if (ce == cudaSuccess) ce = le;
+    }
+    cudaStreamDestroy(cap);
+    if (est == LIFE_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (est != LIFE_OK || ce != cudaSuccess) {
+        *out = nullptr;
+        if (est == LIFE_OK) set_error("building the step graph failed: %s", cudaGetErrorString(ce));
+        return est != LIFE_OK ? est : LIFE_ECUDA;
+    }
+    return LIFE_OK;
+}
 
 life_status build_while_graph(while_body_fn enqueue_body, void* ctx, cudaGraphExec_t* out) {
     *out = nullptr;

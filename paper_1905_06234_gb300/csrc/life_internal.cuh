@@ -240,6 +240,11 @@ struct life_index_s {
     const void* graph_key[8] = {nullptr};
     double graph_tol = -1.0;
     int graph_eq7 = -1;
+    // cached one-step graph (life_sbbnnls_step)
+    cudaGraphExec_t step_graph = nullptr;
+    const void* step_key[8] = {nullptr};
+    double step_tol = -1.0;
+    int step_eq7 = -1;
 };
 
 namespace life {
@@ -303,6 +308,9 @@ life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s);
 // starts at 1 at every launch; the body's last kernel sets it for the next round.
 typedef life_status (*while_body_fn)(void* ctx, cudaStream_t s, cudaGraphConditionalHandle h);
 life_status build_while_graph(while_body_fn enqueue_body, void* ctx, cudaGraphExec_t* out);
+// Drops the index's cached solve and step graphs (after the device is idle): their
+// launches hold the layout's buffers and choices, so a rebuild must drop them.
+void drop_index_graphs(life_index_s* ix);
 // Loop control of a solve graph: loop[0] counts the rounds of a launch, loop[1]
 // holds the round limit; both are set by enqueue_loop_init before each launch.
 life_status enqueue_loop_init(int64_t* loop, int64_t max_iter, cudaStream_t s);
