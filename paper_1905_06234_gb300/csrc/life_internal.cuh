@@ -151,7 +151,7 @@ struct TileLayout {
                              // warp's 32 x 33 Z tile (row-major; atom-major with FP32 storage)
     DevBuf wfl;              // uint16 [n_nnz]: byte offset of the brick-local fascicle in the table
     DevBuf wval;             // bf16 [n_nnz]
-    DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom sub)
+    DevBuf wseg_ptr;         // int32 [n_tiles * 4 * n_sub + 1] offsets per (tile, quarter, 32-atom segment)
     DevBuf fl;               // uint16 [n_nnz]: byte offset of the brick-local fascicle in the weight table
     DevBuf val;              // [n_nnz] stored values: bf16 (vbytes 2) or float (vbytes 4)
     int vbytes = 2;          // bytes per stored value: 2 for BF16 storage, 4 for FP32 storage
@@ -169,7 +169,7 @@ struct TileLayout {
     // WC fixed-point tables: per brick, an upper bound on Σ|val| over the entries of
     // any one brick-local fascicle; per tile, the bits of max |r| over its voxels
     // Live-entry DSC stream (sparse-w-aware DSC): the DSC stream restricted to the
-    // entries of a live set of brick-local fascicles, same (tile, sub-chunk) structure
+    // entries of a live set of brick-local fascicles, same (tile, chunk) structure
     bool sparse = false;     // the index keeps and may use the compacted stream
     DevBuf c_soff, c_fl, c_val;  // uint16, uint16, bf16 [n_nnz padded]
     DevBuf c_chunk_end;      // int32 [n_tiles * kp/128]: each 128-atom chunk's live entries occupy
