@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(256) x_amax_kernel(const float* __restrict__ x
 // The sparse-w-aware DSC (Sec. 4.2.1: an entry whose weight is zero contributes
 // nothing, and SBB-NNLS iterates keep many weights at exactly zero).  Besides the
 // full stream, the index keeps a compacted copy holding only the entries of a
-// live set L of brick-local fascicles, each (tile, 128-atom chunk) in the same
-// place and cell order as in the full stream.  Every DSC call checks on the device whether the input's support
+// live set L of brick-local fascicles, with the same (tile, 32-atom sub-chunk)
+// structure.  Every DSC call checks on the device whether the input's support
 // lies inside L ("stale" otherwise); a small decision kernel then picks the full
 // or the compacted stream for this call, and may rebuild the compacted stream
 // (L := the input's support) when the input is sparse enough and the stored
