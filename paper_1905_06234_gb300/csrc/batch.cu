@@ -193,6 +193,7 @@ static life_status autotune_simt(life_index_s* ix, cudaStream_t s) {
 life_status autotune_tc(life_index_s* ix, cudaStream_t s) {
     if (ix->algo == LIFE_ALGO_SIMT) return autotune_simt(ix, s);
     if (!(ix->algo == LIFE_ALGO_TC && ix->tile.built)) return LIFE_OK;
+    drop_index_graphs(ix);  // cached graphs launch on the layout about to be rebuilt
     const TuneKey key{ilog2(ix->nnz), ilog2(ix->nv), ilog2(ix->nf), ix->nt, ix->na, ix->batch.n,
                       ix->voxel_ijk.p ? 1 : 0};
     int bestB = -1, bestG = 0;

@@ -309,7 +309,8 @@ life_status bounded_wait_probe(int64_t limit_ns, cudaStream_t s);
 typedef life_status (*while_body_fn)(void* ctx, cudaStream_t s, cudaGraphConditionalHandle h);
 life_status build_while_graph(while_body_fn enqueue_body, void* ctx, cudaGraphExec_t* out);
 // Drops the index's cached solve and step graphs (after the device is idle): their
-// launches hold the layout's buffers and choices, so a rebuild must drop them.
+// launches hold the layout's buffers and choices, so the autotuner, which rebuilds
+// an existing index's layout or changes its kernel choice, drops them first.
 void drop_index_graphs(life_index_s* ix);
 // Loop control of a solve graph: loop[0] counts the rounds of a launch, loop[1]
 // holds the round limit; both are set by enqueue_loop_init before each launch.

@@ -626,7 +626,6 @@ static life_status upload(DevBuf& dst, const std::vector<T>& src, cudaStream_t s
 
 life_status build_tile_layout(life_index_s* ix, cudaStream_t s) {
     TileLayout& L = ix->tile;
-    drop_index_graphs(ix);  // cached graphs launch on the layout being replaced
     if (ix->na > 512 || ix->nt > 128) {
         set_error("tensor-core path supports Na <= 512 and Ntheta <= 128 (got %d, %d)", ix->na, ix->nt);
         return LIFE_ENOTSUP;
